@@ -1,0 +1,340 @@
+"""Seeded synthetic inputs for the Matsubara-time GW hot path.
+
+This module is shared by the FP64 CPU oracle and by the GPU library's tests
+and benchmark. It holds only input generation -- random numbers, synthetic
+crystals and the discretisation grid -- and none of the GW arithmetic
+(no Green's function, polarization, screening, self-energy or transform).
+
+Synthetic crystal (stand-in for the paper's FP-LAPW crystals, which are not
+available; the paper's workloads are 4x4x4 k-meshes with >=150 empty bands,
+Sec. "Computational Details"):
+
+* band energies eps[k, b]: eigenvalues of a seeded complex Gaussian Hermitian
+  H_k (Nb x Nb), mapped per k affinely so that the lowest Nocc land on
+  [-1, -0.05] Ha and the rest on [0.05, 1] Ha (0.1 Ha gap at mu = 0; the
+  paper measures energies from mu, Sec. "Green's function in the reference
+  K-S system").
+* Coulomb diagonal v[q, I] = 4 pi / (0.05 + g^2), g ~ U[0, 3]
+  (diagonal like the paper's v_GG'(q) = 4 pi delta_GG' / |q+G|^2).
+* plane-wave matrix elements M^I_ab(k, q) (paper Eq. mmatrix) replaced by
+  complex Gaussian numbers with E|M|^2 = 1/Nb, drawn from Philox4x32-10
+  (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the seed, with the flat index
+  of (q, k, I, a, b) as counter, then Box-Muller. The GPU library implements
+  the same published generator on its own; integer streams are bitwise equal.
+
+Grid (discretisation input, passed explicitly to both sides):
+
+* tau nodes: Gauss-Legendre nodes in s = ln(tau) on [ln tau_min, ln(beta/2)],
+  mirrored to beta - tau, so the set is closed under tau -> beta - tau.
+* real-frequency poles E_l of the fermionic Lehmann kernel
+  K(tau, E) = exp(-E tau) / (1 + exp(-beta E)), chosen by column-pivoted QR
+  over a fine pole set (the discrete Lehmann representation of Kaye, Chen and
+  Parcollet, 2022).
+* bosonic / fermionic Matsubara index sets chosen by pivoted QR over the
+  Lehmann kernel's Matsubara transforms; plus the dense first-N fermionic set
+  used for analytic continuation (the paper uses 128, Sec. "Computational
+  Details").
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+import scipy.linalg as _sl
+
+# ---------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11): multipliers and Weyl key increments.
+# ---------------------------------------------------------------------------
+PHILOX_M0 = np.uint64(0xD2511F53)
+PHILOX_M1 = np.uint64(0xCD9E8D57)
+PHILOX_W0 = np.uint64(0x9E3779B9)
+PHILOX_W1 = np.uint64(0xBB67AE85)
+_MASK32 = np.uint64(0xFFFFFFFF)
+_S32 = np.uint64(32)
+
+# Stream tags used in counter word 2, so that different synthetic tensors
+# never share Philox counters.
+STREAM_M = 0x4D  # plane-wave matrix elements
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox4x32 with 10 rounds on numpy arrays of 32-bit values.
+
+    Each round multiplies counter words 0 and 2 by the two Philox constants,
+    xors the high halves with words 1/3 and the key, and the key is bumped by
+    the Weyl constants between rounds. Returns four uint64 arrays holding
+    32-bit values.
+    """
+    c0 = np.asarray(c0, dtype=np.uint64) & _MASK32
+    c1 = np.asarray(c1, dtype=np.uint64) & _MASK32
+    c2 = np.asarray(c2, dtype=np.uint64) & _MASK32
+    c3 = np.asarray(c3, dtype=np.uint64) & _MASK32
+    k0 = np.uint64(int(k0) & 0xFFFFFFFF)
+    k1 = np.uint64(int(k1) & 0xFFFFFFFF)
+    for _ in range(10):
+        p0 = PHILOX_M0 * c0
+        p1 = PHILOX_M1 * c2
+        hi0, lo0 = p0 >> _S32, p0 & _MASK32
+        hi1, lo1 = p1 >> _S32, p1 & _MASK32
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0), lo1, (hi0 ^ c3 ^ k1), lo0
+        k0 = (k0 + PHILOX_W0) & _MASK32
+        k1 = (k1 + PHILOX_W1) & _MASK32
+    return c0, c1, c2, c3
+
+
+def _u53_open0(hi, lo):
+    """53-bit uniform on (0, 1] from two 32-bit words: (m + 1) * 2^-53."""
+    m = (hi << np.uint64(21)) | (lo >> np.uint64(11))
+    return (m.astype(np.float64) + 1.0) * 2.0 ** -53
+
+
+def _u53(hi, lo):
+    """53-bit uniform on [0, 1) from two 32-bit words: m * 2^-53."""
+    m = (hi << np.uint64(21)) | (lo >> np.uint64(11))
+    return m.astype(np.float64) * 2.0 ** -53
+
+
+TWO_PI = 6.283185307179586  # fp64(2 pi); the GPU generator uses the same literal
+
+
+def m_flat_index(q, k, I, a, b, nk, ni, nb):
+    """Flat Philox counter of element M^I_ab(k, q): ((((q*nk + k)*ni + I)*nb + a)*nb + b)."""
+    return ((((np.uint64(q) * np.uint64(nk) + np.uint64(k)) * np.uint64(ni)
+              + np.asarray(I, np.uint64)) * np.uint64(nb) + np.asarray(a, np.uint64))
+            * np.uint64(nb) + np.asarray(b, np.uint64))
+
+
+def m_values_from_index(idx, seed, nb):
+    """Complex Gaussian M values for flat indices idx (uint64 array).
+
+    counter = (idx mod 2^32, idx div 2^32, STREAM_M, 0), key = (seed lo, seed hi);
+    u1 in (0,1], u2 in [0,1) from 53-bit mantissas; Box-Muller
+    r = sqrt(-2 ln u1), theta = TWO_PI * u2; M = (r cos theta + i r sin theta) / sqrt(2 nb).
+    """
+    idx = np.asarray(idx, dtype=np.uint64)
+    x0, x1, x2, x3 = philox4x32_10(idx & _MASK32, idx >> _S32,
+                                   np.full(idx.shape, STREAM_M, np.uint64),
+                                   np.zeros(idx.shape, np.uint64),
+                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    u1 = _u53_open0(x0, x1)
+    u2 = _u53(x2, x3)
+    r = np.sqrt(-2.0 * np.log(u1))
+    th = TWO_PI * u2
+    s = math.sqrt(0.5 / nb)
+    return (r * np.cos(th)) * s + 1j * ((r * np.sin(th)) * s)
+
+
+def m_block(seed, q, k, nk, ni, nb):
+    """M^I_ab(k, q) for all I, a, b as a complex array [ni, nb, nb].
+
+    Index convention: a is a band at k - q, b a band at k (paper Eq. irpol
+    relabelled k -> k - q, so that the same tensor serves Eq. sigc).
+    """
+    I, a, b = np.meshgrid(np.arange(ni), np.arange(nb), np.arange(nb), indexing="ij")
+    idx = m_flat_index(q, k, I, a, b, nk, ni, nb)
+    return m_values_from_index(idx, seed, nb)
+
+
+# ---------------------------------------------------------------------------
+# Synthetic crystal
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class Crystal:
+    seed: int
+    nk: int
+    nq: int
+    nb: int
+    nocc: int
+    ni: int
+    beta: float
+    eps: np.ndarray        # [nk, nb] float64, Ha, relative to mu = 0, ascending per k
+    v: np.ndarray          # [nq, ni] float64
+    kmq: np.ndarray        # [nq, nk] int32: index of k - q on the k grid
+    qidx: np.ndarray       # [nq] int32: which grid vector each q is
+    mesh: tuple            # (n1, n2, n3) k mesh
+
+    @property
+    def mseed(self):
+        return self.seed
+
+
+def kmesh_shape(nk):
+    n = round(nk ** (1.0 / 3.0))
+    if n ** 3 == nk:
+        return (n, n, n)
+    return (nk, 1, 1)
+
+
+def kminusq_table(mesh, qlist):
+    """k - q on a periodic mesh: k = (i1, i2, i3) flattened row-major."""
+    n1, n2, n3 = mesh
+    nk = n1 * n2 * n3
+    ks = np.array(np.unravel_index(np.arange(nk), mesh)).T
+    out = np.zeros((len(qlist), nk), np.int32)
+    for iq, q in enumerate(qlist):
+        qv = np.array(np.unravel_index(q, mesh))
+        d = (ks - qv[None, :]) % np.array(mesh)[None, :]
+        out[iq] = np.ravel_multi_index(d.T, mesh)
+    return out
+
+
+def make_crystal(seed, nk, nb, nocc, ni, beta, nq=None, qlist=None):
+    """Seeded synthetic crystal; eps from seeded Hermitian H_k (see module doc)."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    mesh = kmesh_shape(nk)
+    eps = np.zeros((nk, nb))
+    for k in range(nk):
+        x = rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
+        h = 0.5 * (x + x.conj().T)
+        lam = np.linalg.eigvalsh(h)
+        lo, hi = lam[:nocc], lam[nocc:]
+        e = np.empty(nb)
+        if nocc > 1:
+            e[:nocc] = -1.0 + (lo - lo[0]) * (0.95 / (lo[-1] - lo[0]))
+        else:
+            e[:nocc] = -0.05
+        if nb - nocc > 1:
+            e[nocc:] = 0.05 + (hi - hi[0]) * (0.95 / (hi[-1] - hi[0]))
+        else:
+            e[nocc:] = 0.05
+        eps[k] = e
+    if qlist is None:
+        qlist = list(range(nk if nq is None else nq))
+    qlist = [int(q) % nk for q in qlist]
+    nq = len(qlist)
+    g = rng.uniform(0.0, 3.0, size=(nq, ni))
+    v = 4.0 * np.pi / (0.05 + g * g)
+    return Crystal(seed=seed, nk=nk, nq=nq, nb=nb, nocc=nocc, ni=ni, beta=float(beta),
+                   eps=eps, v=v, kmq=kminusq_table(mesh, qlist),
+                   qidx=np.array(qlist, np.int32), mesh=mesh)
+
+
+def m_for_q(cr: Crystal, iq: int, ks=None):
+    """M^I_ab(k, q) for the iq-th q and the listed k: complex [len(ks), ni, nb, nb].
+
+    The counter uses the position iq of q in the crystal's q list.
+    """
+    if ks is None:
+        ks = range(cr.nk)
+    return np.stack([m_block(cr.seed, iq, k, cr.nk, cr.ni, cr.nb) for k in ks])
+
+
+# ---------------------------------------------------------------------------
+# Grid
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class Grid:
+    beta: float
+    tau: np.ndarray      # [ntau] ascending, closed under beta - tau
+    wtau: np.ndarray     # [ntau] quadrature weights (sum ~ beta - 2 tau_min)
+    poles: np.ndarray    # [npole] real frequencies of the Lehmann basis
+    nu_idx: np.ndarray   # [nnu] bosonic Matsubara indices n >= 0 (nu_n = 2 n pi / beta)
+    w_idx: np.ndarray    # [nw] fermionic Matsubara indices n >= 0 (w_n = (2n+1) pi / beta)
+    ncont: int           # dense fermionic set n = 0 .. ncont-1 for continuation
+
+    @property
+    def ntau(self):
+        return len(self.tau)
+
+    @property
+    def nnu(self):
+        return len(self.nu_idx)
+
+    @property
+    def nw(self):
+        return len(self.w_idx)
+
+    @property
+    def npole(self):
+        return len(self.poles)
+
+
+def tau_grid_gl_log(beta, ntau, tau_min=1e-3):
+    """Gauss-Legendre nodes in ln(tau) on [tau_min, beta/2], mirrored to beta - tau."""
+    assert ntau % 2 == 0
+    h = ntau // 2
+    x, w = np.polynomial.legendre.leggauss(h)
+    a, b = math.log(tau_min), math.log(beta / 2.0)
+    s = 0.5 * (b - a) * x + 0.5 * (b + a)
+    ws = 0.5 * (b - a) * w
+    t = np.exp(s)
+    wt = ws * t
+    tau = np.concatenate([t, beta - t[::-1]])
+    wtau = np.concatenate([wt, wt[::-1]])
+    return tau, wtau
+
+
+def _kernel_f(tau, E, beta):
+    """Fermionic Lehmann kernel exp(-E tau)/(1+exp(-beta E)), overflow-free (grid selection only)."""
+    tau = np.asarray(tau, float)[:, None]
+    E = np.asarray(E, float)[None, :]
+    a = np.abs(E)
+    den = 1.0 + np.exp(-beta * a)
+    return np.where(E >= 0, np.exp(-a * tau), np.exp(-a * (beta - tau))) / den
+
+
+def select_poles(tau, beta, lam, tol=1e-10, nfine=1500, emin=1e-6):
+    """Column-pivoted QR of K(tau_i, E) over a fine log grid of +-E and 0; keep
+    pivots with |R_jj| > tol |R_00| (at most len(tau))."""
+    ef = np.geomspace(emin, lam, nfine)
+    efine = np.concatenate([-ef[::-1], [0.0], ef])
+    K = _kernel_f(tau, efine, beta)
+    _, R, piv = _sl.qr(K, pivoting=True, mode="economic")
+    d = np.abs(np.diag(R))
+    r = int(np.sum(d > tol * d[0]))
+    return np.sort(efine[piv[:r]])
+
+
+def select_matsubara(poles, beta, nsel, fermionic, nmax):
+    """Pivoted QR over n = 0..nmax of the Lehmann kernel's Matsubara transform
+    columns; returns the first nsel pivots, sorted."""
+    n = np.arange(nmax + 1)
+    z = 1j * ((2 * n + 1) if fermionic else (2 * n)) * np.pi / beta
+    E = np.asarray(poles)[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if fermionic:
+            Kh = -1.0 / (z[:, None] - E)
+        else:
+            Kh = -np.tanh(0.5 * beta * E) / (z[:, None] - E)
+            Kh = np.where((n[:, None] == 0) & (E == 0), 0.5 * beta, Kh)
+    _, _, piv = _sl.qr(Kh.T, pivoting=True, mode="economic")
+    nsel = min(nsel, len(piv))
+    return np.sort(n[piv[:nsel]]).astype(np.int32)
+
+
+def make_grid(beta, ntau, nnu, nw, ncont=128, tau_min=1e-3, lam=None, tol=1e-10):
+    tau, wtau = tau_grid_gl_log(beta, ntau, tau_min)
+    if lam is None:
+        lam = 1.0 / tau_min
+    poles = select_poles(tau, beta, lam, tol)
+    nmax = int(math.ceil(2.0 * beta * lam / (2.0 * math.pi)))
+    nu_idx = select_matsubara(poles, beta, nnu, False, nmax)
+    w_idx = select_matsubara(poles, beta, nw, True, nmax)
+    return Grid(beta=float(beta), tau=tau, wtau=wtau, poles=poles, nu_idx=nu_idx,
+                w_idx=w_idx, ncont=int(ncont))
+
+
+# ---------------------------------------------------------------------------
+# Workload configurations (synthetic stand-ins for the paper's crystals)
+# ---------------------------------------------------------------------------
+CONFIGS = {
+    # one q, Nk=8, Nb=16 (8 occ), NI=64, Ntau=16, beta=100
+    "c1": dict(seed=1001, nk=8, nb=16, nocc=8, ni=64, beta=100.0, ntau=16, nnu=16, nw=16,
+               qlist=[1]),
+    # Nk=64 (4x4x4), q on the same grid, Nb=64 (32 occ), NI=256, Ntau=48, beta=200
+    "c2": dict(seed=2001, nk=64, nb=64, nocc=32, ni=256, beta=200.0, ntau=48, nnu=48, nw=48,
+               qlist=None),
+    # Nk=216 (6x6x6), Nb=128 (48 occ), NI=512, Ntau=64, beta=400
+    "c3": dict(seed=3001, nk=216, nb=128, nocc=48, ni=512, beta=400.0, ntau=64, nnu=64, nw=64,
+               qlist=None),
+}
+
+
+def make_config(name, **over):
+    c = dict(CONFIGS[name])
+    c.update(over)
+    cr = make_crystal(c["seed"], c["nk"], c["nb"], c["nocc"], c["ni"], c["beta"],
+                      qlist=c["qlist"] if c["qlist"] is not None else list(range(c["nk"])))
+    gr = make_grid(c["beta"], c["ntau"], c["nnu"], c["nw"], ncont=c.get("ncont", 128))
+    return cr, gr

@@ -1,0 +1,34 @@
+"""FP64 CPU oracle for the Matsubara-time GW hot path (test infrastructure).
+
+This package is the independent reference that the GPU library is checked
+against. It is test infrastructure only: the tests, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the GPU library and its
+Python binding never do. It shares no code with the library: only the seeded
+input generators in ``gwinputs`` serve both sides.
+
+Every function cites the passage of Chu et al., "All-electron self-consistent
+GW in the Matsubara-time domain" (arXiv:1602.02313) that it follows.
+
+Parity status per function (what pins it; see tests/test_oracle_*.py):
+
+* green_tau0        -- closed form of the reference G0 (Sec. III.B.1), pinned by
+                       boundary values and particle number.
+* polarization      -- Eq. (irpol), pinned by the Lindhard closed form of its
+                       Matsubara transform, Hermiticity and P(tau) <= 0.
+* transforms        -- Lehmann-basis least squares; pinned by exactness on
+                       basis functions and by closed-form transforms of G0.
+* screen            -- iν form of Eq. (tildeW); pinned by the one-mode secular
+                       closed form and the residual of the linear system.
+* selfenergy        -- Eq. (sigc) and the product-basis form of Eq. (sigx);
+                       pinned by brute-force Matsubara convolution on tiny
+                       inputs and the direct occupied-state sum.
+* dyson_iw          -- diagonal Dyson (Eqs. dysongf-zcjk) posed in iω; pinned
+                       by the zero and static self-energy closed forms.
+* pade / cpe / qp   -- analytic continuation (Sec. III.B.6); pinned by exact
+                       recovery of few-pole models and causality.
+* mlp               -- not in the paper; pinned by central finite differences.
+"""
+from .gw import *  # noqa: F401,F403
+from .transforms import transform_matrices  # noqa: F401
+from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
+                           qp_solve, band_gap)

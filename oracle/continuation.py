@@ -1,0 +1,117 @@
+"""Analytic continuation and quasiparticle energies (Sec. III.B.6), FP64, plain
+loops (test infrastructure; see the package docstring).
+
+* Pade: Vidberg-Serene continued fraction (J. Low Temp. Phys. 29, 179 (1977)),
+  the comparison method named in the paper.
+* CPE: continuous-pole expansion (Staar et al. 2014, the paper's Eqs. after
+  Eq. trans): Im Sigma(w + i eta) is piecewise linear on a real grid with
+  coefficients of fixed sign (causality, Im Sigma <= 0), so
+  Sigma(z) = sum_m b_m Phi_m(z),  b_m >= 0,  Phi_m(z) = int h_m(x) / (z - x) dx
+  with h_m the hat function at node x_m. The b are the non-negative
+  least-squares minimisers of sum_n |Sigma~(i w_n) - Sigma(i w_n)|^2
+  (Lawson-Hanson NNLS via SciPy).
+* QP: root of E - eps - Sigma^x + Sigma_0 - Re Sigma^c(E) = 0 nearest eps
+  (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where this vanishes).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.optimize as _so
+
+
+# ---------------------------------------------------------------- Pade
+def pade_coeffs(z, u):
+    """Continued-fraction coefficients a_p from points z_p and values u_p:
+    g_1(z_i) = u_i; g_p(z_i) = (g_{p-1}(z_{p-1}) - g_{p-1}(z_i)) / ((z_i - z_{p-1}) g_{p-1}(z_i));
+    a_p = g_p(z_p)."""
+    z = np.asarray(z, complex)
+    g = np.array(u, complex)
+    n = len(z)
+    a = np.zeros(n, complex)
+    a[0] = g[0]
+    for p in range(1, n):
+        prev = g[p - 1]
+        for i in range(p, n):
+            g[i] = (prev - g[i]) / ((z[i] - z[p - 1]) * g[i])
+        a[p] = g[p]
+    return a
+
+
+def pade_eval(a, z, x):
+    """C(x) = a_1 / (1 + a_2 (x - z_1) / (1 + a_3 (x - z_2) / (1 + ...))), bottom-up."""
+    x = np.asarray(x, complex)
+    n = len(a)
+    t = np.ones_like(x)
+    for p in range(n - 1, 0, -1):
+        t = 1.0 + a[p] * (x - z[p - 1]) / t
+    return a[0] / t
+
+
+# ---------------------------------------------------------------- CPE
+def cpe_grid(nhat=128, xmin=0.01, xmax=200.0):
+    """Real-frequency nodes x_0 < ... < x_{nhat+1}: +-geomspace(xmin, xmax, nhat/2)
+    plus end nodes +-xmax * r (r the geometric ratio); hats sit on the nhat
+    interior nodes and vanish at the two end nodes."""
+    h = nhat // 2
+    g = np.geomspace(xmin, xmax, h)
+    r = g[1] / g[0]
+    x = np.concatenate([[-xmax * r], -g[::-1], g, [xmax * r]])
+    return x
+
+
+def cpe_kernel(x, z):
+    """Phi_m(z) = int h_m(s)/(z - s) ds for hats on interior nodes x_1..x_M.
+
+    Rising part on [x0, x1] (h = x1 - x0): ((z - x0)/h) (log(z - x0) - log(z - x1)) - 1.
+    Falling part on [x1, x2] (h' = x2 - x1): ((x2 - z)/h') (log(z - x1) - log(z - x2)) + 1.
+    Principal logs; z in the upper half plane (or real, taken from above).
+    Returns [len(z), M] complex."""
+    z = np.asarray(z, complex)[:, None]
+    x0, x1, x2 = x[None, :-2], x[None, 1:-1], x[None, 2:]
+    l0 = np.log(z - x0)
+    l1 = np.log(z - x1)
+    l2 = np.log(z - x2)
+    rise = (z - x0) / (x1 - x0) * (l0 - l1) - 1.0
+    fall = (x2 - z) / (x2 - x1) * (l1 - l2) + 1.0
+    return rise + fall
+
+
+def cpe_fit(w, sig, x):
+    """b >= 0 minimising sum_n |sig_n - sum_m b_m Phi_m(i w_n)|^2. Returns (b, residual norm)."""
+    K = cpe_kernel(x, 1j * np.asarray(w))
+    A = np.vstack([K.real, K.imag])
+    y = np.concatenate([np.asarray(sig).real, np.asarray(sig).imag])
+    b, res = _so.nnls(A, y, maxiter=50 * A.shape[1])
+    return b, res
+
+
+def cpe_eval(b, x, z):
+    return cpe_kernel(x, z) @ b
+
+
+# ---------------------------------------------------------------- QP
+def qp_solve(eps, sigx, vxc, resig, de=1e-6, tol=1e-12, maxit=100):
+    """Quasiparticle energy: root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E)
+    nearest eps by secant/Newton iteration from E = eps (resig(E) returns
+    Re Sigma^c at real E). Returns (E, Z, ok)."""
+    E = float(eps)
+    ok = False
+    for _ in range(maxit):
+        F = E - eps - sigx + vxc - resig(E)
+        dF = 1.0 - (resig(E + de) - resig(E - de)) / (2 * de)
+        if dF == 0 or not np.isfinite(dF):
+            break
+        step = F / dF
+        step = max(-0.5, min(0.5, step))
+        E -= step
+        if abs(step) < tol * max(1.0, abs(E)):
+            ok = True
+            break
+    dS = (resig(E + de) - resig(E - de)) / (2 * de)
+    return E, 1.0 / (1.0 - dS), ok
+
+
+def band_gap(E, nocc):
+    """min_k E[k, nocc] - max_k E[k, nocc-1] (0-based band index)."""
+    E = np.asarray(E)
+    return E[:, nocc].min() - E[:, nocc - 1].max()
