@@ -1,0 +1,189 @@
+/*
+ * gw.h -- C ABI of libgw, the GB300 (sm_103a) hot path of the Matsubara-time
+ * GW cycle of Chu et al., "All-electron self-consistent GW in the
+ * Matsubara-time domain" (arXiv:1602.02313), Sec. III.B.
+ *
+ * Conventions (all entry points):
+ *  - The caller owns every buffer. Array arguments are DEVICE pointers unless
+ *    marked "host". Nothing is returned to the host inside the per-q chain.
+ *  - Complex numbers are interleaved (re, im) FP64 pairs ("cplx" below).
+ *    Arrays are row-major with the shape given in brackets.
+ *  - Energies are in Ha and measured from the chemical potential mu = 0
+ *    (Sec. III.B.1); beta is in 1/Ha.
+ *  - Band-pair convention: M[q][k][I][a][b] = M^I_ab(k, q) with band a at
+ *    k - q and band b at k. This is Eq. (mmatrix) with k relabelled k -> k - q,
+ *    so the same tensor serves Eq. (irpol) (P) and Eq. (sigc) (Sigma^c).
+ *  - Calls are asynchronous and ordered on the stream given to gw_create.
+ *    Argument errors are returned immediately (GW_EINVAL); a CUDA launch
+ *    error is returned as GW_ECUDA; errors of asynchronous work surface at the
+ *    next call or at gw_sync. gw_last_error() gives a readable message.
+ *  - There is no CPU fallback: every step runs in libgw's CUDA kernels.
+ *  - A context must not be used from two host threads at once.
+ */
+#ifndef GW_H
+#define GW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gw_ctx gw_ctx;
+
+typedef enum {
+  GW_OK = 0,
+  GW_EINVAL = -1,        /* bad argument (null pointer, size out of range) */
+  GW_ENOMEM = -2,        /* device allocation failed */
+  GW_ECUDA = -3,         /* CUDA runtime error */
+  GW_ESINGULAR = -4,     /* zero pivot in a dielectric solve (see info[]) */
+  GW_ENOCONV = -5,       /* continuation / QP iteration did not converge (see info[]) */
+  GW_ETIMEOUT = -6,      /* a bounded device-side wait ran out */
+  GW_EUNSUPPORTED = -7   /* combination not built (e.g. precision for this size) */
+} gw_status;
+
+/* Arithmetic of the P and Sigma^c contractions. */
+typedef enum {
+  GW_FP64 = 0,    /* native FP64 (CUDA cores); the parity path */
+  GW_FP16X2 = 1,  /* tcgen05 tensor cores: fp16 hi/lo split operands, 3 products, FP32 TMEM accumulation */
+  GW_BF16X3 = 2   /* tcgen05 tensor cores: bf16 three-slice split, 6 products, FP32 TMEM accumulation */
+} gw_prec;
+
+typedef enum { GW_BOSE = 0, GW_FERMI = 1 } gw_stat;
+
+typedef enum {
+  GW_TAU_TO_IW = 0,       /* tau -> sparse Matsubara set (nu_idx or w_idx) */
+  GW_IW_TO_TAU = 1,       /* sparse Matsubara set -> tau */
+  GW_TAU_TO_IW_CONT = 2   /* FERMI only: tau -> dense set w_n, n = 0 .. ncont-1 */
+} gw_dir;
+
+typedef enum { GW_PADE = 0, GW_CPE = 1 } gw_cont_method;
+
+/* Discretisation (all host arrays, copied by gw_create). */
+typedef struct {
+  double beta;            /* inverse temperature, 1/Ha */
+  int ntau;               /* number of tau nodes (even) */
+  const double* tau;      /* host [ntau]: ascending in (0, beta), closed under tau -> beta - tau */
+  int npole;              /* Lehmann basis size, 1 <= npole <= ntau */
+  const double* poles;    /* host [npole]: real frequencies E_l of the basis exp(-E tau)/(1+exp(-beta E)) */
+  int nnu;                /* bosonic sparse set size */
+  const int* nu_idx;      /* host [nnu]: n >= 0, nu_n = 2 n pi / beta */
+  int nw;                 /* fermionic sparse set size */
+  const int* w_idx;       /* host [nw]: n >= 0, w_n = (2 n + 1) pi / beta */
+  int ncont;              /* dense fermionic set n = 0 .. ncont-1 for continuation (<= 512) */
+} gw_grid;
+
+/* Synthetic crystal. */
+typedef struct {
+  uint64_t seed;          /* key of the Philox4x32-10 stream of M */
+  int nk;                 /* k points (q runs over nq of them) */
+  int nq;                 /* q points handled by this context */
+  int nb;                 /* bands per k (<= 256) */
+  int nocc;               /* occupied bands (used only for reporting) */
+  int ni;                 /* product-basis size (multiple of 32, <= 1024) */
+  double omega;           /* unit-cell volume Omega in 1/(Omega N_k) of Eqs. irpol, sigc */
+  const int* kmq;         /* host [nq][nk]: index of k - q */
+  const double* v;        /* host [nq][ni]: diagonal Coulomb v_I(q) > 0 */
+  const double* M;        /* device cplx [nq][nk][ni][nb][nb], or NULL: libgw generates M
+                             from seed (Philox4x32-10, counter = flat index of (q,k,I,a,b),
+                             Box-Muller, E|M|^2 = 1/nb) and keeps it in its own HBM buffer */
+} gw_system;
+
+/* Create a context on `device`, ordered on the cudaStream_t `stream` (NULL =
+ * legacy default stream). Builds the tau <-> Matsubara transform matrices
+ * (Lehmann-basis least squares, formed in double-double arithmetic) and, when
+ * sys->M is NULL, allocates nq*nk*ni*nb*nb*16 bytes of HBM and generates M.
+ * Returns GW_EINVAL for inconsistent sizes, GW_ENOMEM if HBM runs out. */
+gw_status gw_create(gw_ctx** ctx, const gw_grid* grid, const gw_system* sys, int device,
+                    void* stream);
+gw_status gw_destroy(gw_ctx* ctx);
+gw_status gw_sync(gw_ctx* ctx);
+const char* gw_last_error(gw_ctx* ctx);
+
+/* Green's function on the tau grid.
+ * sigx, vxc, sigc_iw all NULL: reference G0_j(k|tau) = -exp(-eps tau)[1 - n_F(eps)]
+ *   (Sec. III.B.1), evaluated without overflow; occ = n_F(eps) = G(0^-) = -G(beta^-).
+ * otherwise: diagonal Dyson update (Eqs. dysongf, zxjk, zcjk) posed at the sparse
+ *   fermionic set: G(i w) = 1/(i w - eps - sigx + vxc - sigc_iw(i w)); the pole
+ *   1/(i w - eps~), eps~ = eps + sigx - vxc, is subtracted and added back exactly in tau.
+ * eps [nk][nb]; sigx, vxc [nk][nb]; sigc_iw cplx [nk][nb][nw];
+ * G_tau out [nk][nb][ntau]; occ out [nk][nb]. */
+gw_status gw_green_tau(gw_ctx* ctx, const double* eps, const double* sigx, const double* vxc,
+                       const double* sigc_iw, double* G_tau, double* occ);
+
+/* Irreducible polarization of the iq-th q, Eq. (irpol):
+ * P_II'(q|tau) = 1/(Omega N_k) sum_k sum_ab M^I_ab Q_ab(tau) conj(M^I'_ab),
+ * Q_ab(tau) = G_b(k|tau) G_a(k-q|-tau), G(-tau) = -G(beta - tau) (Sec. II).
+ * G_tau [nk][nb][ntau] (any G: G0 or dressed); P_tau out cplx [ntau][ni][ni] (Hermitian). */
+gw_status gw_polarization(gw_ctx* ctx, int iq, const double* G_tau, gw_prec prec, double* P_tau);
+
+/* Imaginary time <-> Matsubara transforms (Eq. trans and its bosonic / inverse
+ * counterparts), fixed FP64 matrices applied as batched matvecs.
+ *  BOSE  TAU_TO_IW : in cplx [ntau][batch]        -> out cplx [nnu][batch]
+ *  BOSE  IW_TO_TAU : in cplx [nnu][m][m] of a Hermitian-matrix function (batch = m)
+ *                    -> out cplx [ntau][m][m]; uses W(-i nu) = W(i nu)^dagger
+ *  FERMI TAU_TO_IW : in real [batch][ntau]        -> out cplx [batch][nw]
+ *  FERMI TAU_TO_IW_CONT : in real [batch][ntau]   -> out cplx [batch][ncont]
+ *  FERMI IW_TO_TAU : in cplx [batch][nw] of a real tau-function -> out real [batch][ntau] */
+gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, const double* in,
+                         double* out);
+
+/* Screened interaction minus bare Coulomb, W~ = W - v (Sec. III.B.3), at the bosonic
+ * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2,
+ * solve (1 - Pi) X = Pi by LU without pivoting (1 - Pi has Hermitian part >= 1),
+ * W~ = v^1/2 X v^1/2, for the nqb q points iq0 .. iq0 + nqb - 1 at once.
+ * P_iv, Wt_iv cplx [nqb][nnu][ni][ni]; info out (device) [nqb][nnu]: 0, or j+1 for a
+ * zero pivot at elimination step j (that system's output is then undefined).
+ * Uses nqb * nnu * ni * 2 ni * 16 bytes of workspace that the context allocates
+ * (and grows) on first use. */
+gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, double* Wt_iv, int* info);
+
+/* Contribution of the iq-th q to the self-energy, ACCUMULATED into the outputs:
+ * Eq. (sigc): Sigc_n(k|tau) += -1/(Omega N_k) sum_j G_j(k-q|tau) a_jn^dagger W~(q|tau) a_jn,
+ *             a_jn = M[q][k][:][j][n];
+ * Eq. (sigx) in the product basis with diagonal v:
+ *             Sigx_n(k) += -1/(Omega N_k) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2.
+ * G_tau [nk][nb][ntau]; occ [nk][nb]; Wt_tau cplx [ntau][ni][ni] (Hermitian);
+ * Sigc_tau [nk][nb][ntau] (real: W~(tau) Hermitian); Sigx [nk][nb] (may be NULL). */
+gw_status gw_selfenergy(gw_ctx* ctx, int iq, const double* G_tau, const double* occ,
+                        const double* Wt_tau, gw_prec prec, double* Sigc_tau, double* Sigx);
+
+/* Analytic continuation and quasiparticle energies (Sec. III.B.6), one problem per (k, n).
+ * sig_iw cplx [nprob][ncont]: Sigma^c at w_n, n = 0 .. ncont-1.
+ * method GW_PADE: Vidberg-Serene continued fraction through the first npade points
+ *   (npade = min(ncont, 64)).
+ * method GW_CPE : continuous-pole expansion, Im Sigma piecewise linear on the real grid
+ *   x_m (host [ngrid+2], hats on the ngrid interior nodes), b_m >= 0 fitted by
+ *   Lawson-Hanson NNLS with a ridge lambda^2 |b|^2, lambda = ridge * ||A||_F.
+ *   b0 (device [nprob][ngrid] or NULL) warm-starts the active set (learned seed).
+ * eps, sigx, vxc [nprob]: QP root of E - eps - sigx + vxc - Re Sigma^c(E) nearest eps.
+ * omega_real [nreal] (device); sig_real out cplx [nprob][nreal] at omega + i eta (eta = 1e-4);
+ * e_qp out [nprob]; info out [nprob] (0 ok, 1 QP not converged, 2 NNLS iteration cap). */
+gw_status gw_continue(gw_ctx* ctx, gw_cont_method method, int64_t nprob, const double* sig_iw,
+                      const double* eps, const double* sigx, const double* vxc, int nreal,
+                      const double* omega_real, double* sig_real, double* e_qp, int* info);
+
+/* Real-axis grid of the continuous-pole expansion used by gw_continue(GW_CPE):
+ * x host [ngrid + 2] ascending, ridge relative Tikhonov weight (>= 0). Must be
+ * called before the first GW_CPE call; builds A^T A on the device. */
+gw_status gw_cpe_setup(gw_ctx* ctx, int ngrid, const double* x, double ridge);
+/* CPE coefficients of the last gw_continue(GW_CPE) call: b out [nprob][ngrid]. */
+gw_status gw_cpe_coeffs(gw_ctx* ctx, double* b);
+
+/* Matrix elements the context uses (for inspection and tests): copies
+ * M[iq][k][:][:][:] for k in [k0, k0 + nk_copy) into out cplx [nk_copy][ni][nb][nb]. */
+gw_status gw_copy_m(gw_ctx* ctx, int iq, int k0, int nk_copy, double* out);
+
+/* Host-only (no GPU needed): the transform matrices gw_create builds for `grid`,
+ * written to host arrays (NULL entries skipped):
+ * B_fwd cplx [nnu][ntau], F_fwd cplx [nw][ntau], F_cont cplx [ncont][ntau],
+ * B_bwd real [ntau][2*nnu] (columns: Re-part weights, then Im-part weights),
+ * F_bwd real [ntau][2*nw]. Returns GW_EINVAL for an inconsistent grid. */
+gw_status gw_transform_matrices(const gw_grid* grid, double* B_fwd, double* F_fwd, double* F_cont,
+                                double* B_bwd, double* F_bwd);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_H */

@@ -76,17 +76,34 @@ def cpe_kernel(x, z):
     return rise + fall
 
 
-def cpe_fit(w, sig, x):
-    """b >= 0 minimising sum_n |sig_n - sum_m b_m Phi_m(i w_n)|^2. Returns (b, residual norm)."""
+def cpe_fit(w, sig, x, ridge=0.0):
+    """b >= 0 minimising sum_n |sig_n - sum_m b_m Phi_m(i w_n)|^2 + lambda^2 |b|^2,
+    lambda = ridge * ||A||_F (A the real-stacked kernel; ridge = 0 is the plain CPE
+    norm). Solved as NNLS on the stacked matrix [A; lambda I]. Returns (b, residual norm)."""
     K = cpe_kernel(x, 1j * np.asarray(w))
     A = np.vstack([K.real, K.imag])
     y = np.concatenate([np.asarray(sig).real, np.asarray(sig).imag])
+    if ridge > 0:
+        lam = ridge * np.linalg.norm(A)
+        A = np.vstack([A, lam * np.eye(A.shape[1])])
+        y = np.concatenate([y, np.zeros(A.shape[1])])
     b, res = _so.nnls(A, y, maxiter=50 * A.shape[1])
     return b, res
 
 
 def cpe_eval(b, x, z):
     return cpe_kernel(x, z) @ b
+
+
+ETA = 1e-4  # real-axis offset (Ha) at which continued self-energies are evaluated
+
+
+def pade_resig(a, z):
+    return lambda E: pade_eval(a, z, np.array([E + 1j * ETA]))[0].real
+
+
+def cpe_resig(b, x):
+    return lambda E: (cpe_kernel(x, np.array([E + 1j * ETA])) @ b)[0].real
 
 
 # ---------------------------------------------------------------- QP

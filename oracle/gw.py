@@ -48,20 +48,22 @@ def green_iw0(eps, w_idx, beta):
     return 1.0 / (1j * w[None, None, :] - np.asarray(eps)[..., None])
 
 
-def polarization(M, G, kmq, omega=1.0):
+def polarization(M, G, kmq, omega=1.0, its=None):
     """Irreducible polarization for one q, Eq. (irpol):
 
     P_II'(q|tau) = 1/(Omega N_k) sum_k sum_ab M^I_ab Q_ab(k, q|tau) conj(M^I'_ab),
     Q_ab = G_b(k|tau) G_a(k - q|-tau),  G(-tau) = -G(beta - tau)  (Sec. II),
 
     M: [nk, ni, nb, nb] complex (a at k - q, b at k); G: [nk, nb, ntau] real;
-    kmq: [nk] index of k - q. Spin factor 1 (spinor M). Returns [ntau, ni, ni].
+    kmq: [nk] index of k - q. Spin factor 1 (spinor M). Returns [ntau, ni, ni]
+    (or [len(its), ni, ni] for the tau indices its).
     """
     nk, ni, nb, _ = M.shape
     ntau = G.shape[-1]
     mir = mirror_index(ntau)
-    P = np.zeros((ntau, ni, ni), complex)
-    for i in range(ntau):
+    its = list(range(ntau)) if its is None else list(its)
+    P = np.zeros((len(its), ni, ni), complex)
+    for o, i in enumerate(its):
         acc = np.zeros((ni, ni), complex)
         for k in range(nk):
             Gb = G[k, :, i]                       # G_b(k|tau)
@@ -69,7 +71,7 @@ def polarization(M, G, kmq, omega=1.0):
             Q = Ga_m[:, None] * Gb[None, :]       # [a, b]
             A = M[k].reshape(ni, nb * nb)
             acc += (A * Q.reshape(-1)[None, :]) @ A.conj().T
-        P[i] = acc / (omega * nk)
+        P[o] = acc / (omega * nk)
     return P
 
 
@@ -125,7 +127,7 @@ def screen(P_iv, v):
     return out
 
 
-def selfenergy(M, G, W_tau, v, kmq, occ, omega=1.0):
+def selfenergy(M, G, W_tau, v, kmq, occ, omega=1.0, ks=None, its=None):
     """Contribution of one q to the correlation and exchange self-energies.
 
     Eq. (sigc): Sigma^c_n(k|tau) = -1/(Omega N_k) sum_GG' sum_j
@@ -134,15 +136,19 @@ def selfenergy(M, G, W_tau, v, kmq, occ, omega=1.0):
                 Sigma^x_n(k) = -1/(Omega N_k) sum_j f_j(k-q) sum_I v_I |M^I_jn|^2.
     M [nk, ni, nb, nb] (j = a at k - q, n = b at k); G [nk, nb, ntau];
     W_tau [ntau, ni, ni]; occ [nk, nb]. Returns (Sigc [nk, nb, ntau] real,
-    Sigx [nk, nb]).
+    Sigx [nk, nb]); ks / its restrict the k points and tau indices computed
+    (M then holds only those k: M[len(ks), ...], W_tau all tau).
     """
-    nk, ni, nb, _ = M.shape
+    nkm, ni, nb, _ = M.shape
+    nk = G.shape[0]
     ntau = G.shape[-1]
+    ks = list(range(nk)) if ks is None else list(ks)
+    its = list(range(ntau)) if its is None else list(its)
     sc = np.zeros((nk, nb, ntau), complex)
     sx = np.zeros((nk, nb))
-    for k in range(nk):
-        A = M[k].reshape(ni, nb * nb)            # column (a, n)
-        for i in range(ntau):
+    for m_, k in enumerate(ks):
+        A = M[m_].reshape(ni, nb * nb)           # column (a, n)
+        for i in its:
             d = np.einsum("Ip,IJ,Jp->p", A.conj(), W_tau[i], A).reshape(nb, nb)  # [a, n]
             sc[k, :, i] = -(G[kmq[k], :, i][:, None] * d).sum(0) / (omega * nk)
         vm = (np.asarray(v)[:, None] * np.abs(A) ** 2).sum(0).reshape(nb, nb)

@@ -1,0 +1,563 @@
+// libgw: C ABI entry points, context management and the light kernels
+// (matrix-element generator, Green's function, Dyson update, transforms, exchange).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "gw_internal.h"
+
+namespace gwi {
+
+gw_status set_err(gw_ctx* c, gw_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+gw_status check_launch(gw_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(c, GW_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return GW_OK;
+}
+
+// ----------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller: synthetic
+// matrix elements M^I_ab(k, q) with E|M|^2 = 1/nb (stand-in for Eq. mmatrix).
+// counter = (idx lo, idx hi, 0x4D, 0), key = (seed lo, seed hi), idx the flat
+// index of (q, k, I, a, b); u1 = (m1 + 1) 2^-53, u2 = m2 2^-53 from 53-bit words.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                              uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+}
+
+__global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t seed, double scale) {
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < n;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t c0 = (uint32_t)idx, c1 = (uint32_t)(idx >> 32), c2 = 0x4Du, c3 = 0u;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t m1 = ((uint64_t)c0 << 21) | (c1 >> 11);
+    const uint64_t m2 = ((uint64_t)c2 << 21) | (c3 >> 11);
+    const double u1 = ((double)m1 + 1.0) * 0x1p-53;
+    const double u2 = (double)m2 * 0x1p-53;
+    const double r = sqrt(-2.0 * log(u1));
+    const double th = 6.283185307179586 * u2;
+    double s, co;
+    sincos(th, &s, &co);
+    M[idx] = make_double2(r * co * scale, r * s * scale);
+  }
+}
+
+gw_status launch_gen_m(gw_ctx* c, double* M) {
+  const uint64_t n = (uint64_t)c->nq * c->nk * c->ni * c->nb * c->nb;
+  k_gen_m<<<152 * 8, 256, 0, c->stream>>>((double2*)M, n, c->seed, std::sqrt(0.5 / c->nb));
+  return check_launch(c, "gen_m");
+}
+
+// ----------------------------------------------------------------------------
+// Reference Green's function G0_j(k|tau) = -exp(-eps tau)[1 - n_F(eps)] (Sec. III.B.1):
+// eps > 0: -exp(-eps tau)/(1 + exp(-beta eps)); eps <= 0: -exp(eps(beta - tau))/(1 + exp(beta eps)).
+// occ = n_F(eps) = -G(beta^-).
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ double g0_tau(double e, double t, double beta) {
+  const double a = fabs(e);
+  const double den = 1.0 + exp(-beta * a);
+  return e > 0 ? -exp(-a * t) / den : -exp(-a * (beta - t)) / den;
+}
+__device__ __forceinline__ double fermi(double e, double beta) {
+  const double x = exp(-beta * fabs(e));
+  return e > 0 ? x / (1.0 + x) : 1.0 / (1.0 + x);
+}
+
+__global__ void k_green0(const double* __restrict__ eps, const double* __restrict__ tau, int nkb, int ntau,
+                         double beta, double* __restrict__ G, double* __restrict__ occ) {
+  const int64_t n = (int64_t)nkb * ntau;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int kb = (int)(i / ntau), it = (int)(i % ntau);
+    const double e = eps[kb];
+    G[i] = g0_tau(e, tau[it], beta);
+    if (it == 0 && occ) occ[kb] = fermi(e, beta);
+  }
+}
+
+gw_status launch_green0(gw_ctx* c, const double* eps, double* G, double* occ) {
+  const int nkb = c->nk * c->nb;
+  const int64_t n = (int64_t)nkb * c->ntau;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_green0<<<blocks, 256, 0, c->stream>>>(eps, c->d_tau, nkb, c->ntau, c->beta, G, occ);
+  return check_launch(c, "green0");
+}
+
+// ----------------------------------------------------------------------------
+// Diagonal Dyson update in i w (Eqs. dysongf, zxjk, zcjk posed at the sparse fermionic set):
+// G(i w_j) = 1/(i w_j - eps~ - sigc(i w_j)), eps~ = eps + sigx - vxc;
+// R_j = G(i w_j) - 1/(i w_j - eps~);  G(tau_i) = G0(eps~, tau_i) + sum_j A_ij Re R_j + B_ij Im R_j;
+// occ = n_F(eps~) - sum_j (Abeta_j Re R_j + Bbeta_j Im R_j).  One thread per (k, band).
+// ----------------------------------------------------------------------------
+__global__ void k_dyson(const double* __restrict__ eps, const double* __restrict__ sigx,
+                        const double* __restrict__ vxc, const double2* __restrict__ sigc, int nkb,
+                        const double* __restrict__ tau, int ntau, int nw, const int* __restrict__ widx,
+                        double beta, const double* __restrict__ Fbwd,
+                        const double* __restrict__ Fbeta, double* __restrict__ G, double* __restrict__ occ) {
+  const int kb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kb >= nkb) return;
+  const double et = eps[kb] + (sigx ? sigx[kb] : 0.0) - (vxc ? vxc[kb] : 0.0);
+  double* g = G + (size_t)kb * ntau;
+  for (int i = 0; i < ntau; ++i) g[i] = g0_tau(et, tau[i], beta);
+  double ob = 0.0;
+  for (int j = 0; j < nw; ++j) {
+    const double w = (2.0 * widx[j] + 1.0) * 3.141592653589793 / beta;
+    double rr = 0.0, ri = 0.0;
+    if (sigc) {
+      const double2 s = sigc[(size_t)kb * nw + j];
+      // 1/(i w - et - s) - 1/(i w - et)
+      const double ar = -et - s.x, ai = w - s.y;
+      const double d1 = ar * ar + ai * ai;
+      const double br = -et, bi = w;
+      const double d2 = br * br + bi * bi;
+      rr = ar / d1 - br / d2;
+      ri = -ai / d1 + bi / d2;
+    }
+    for (int i = 0; i < ntau; ++i) g[i] += Fbwd[(size_t)i * 2 * nw + j] * rr + Fbwd[(size_t)i * 2 * nw + nw + j] * ri;
+    ob += Fbeta[j] * rr + Fbeta[nw + j] * ri;
+  }
+  occ[kb] = fermi(et, beta) - ob;
+}
+
+gw_status launch_dyson(gw_ctx* c, const double* eps, const double* sigx, const double* vxc,
+                       const double* sigc_iw, double* G, double* occ) {
+  const int nkb = c->nk * c->nb;
+  k_dyson<<<(nkb + 127) / 128, 128, 0, c->stream>>>(eps, sigx, vxc, (const double2*)sigc_iw, nkb, c->d_tau,
+                                                   c->ntau, c->nw, c->d_widx, c->beta, c->d_Fbwd, c->d_Fbwd_beta, G,
+                                                   occ);
+  return check_launch(c, "dyson");
+}
+
+// ----------------------------------------------------------------------------
+// Transforms: fixed FP64 matrices applied as batched matvecs.
+// ----------------------------------------------------------------------------
+// BOSE tau -> i nu: out[j][b] = sum_i T[j][i] in[i][b]  (complex T, complex data)
+template <int JB>
+__global__ void k_bose_fwd(const double2* __restrict__ T, const double2* __restrict__ in, double2* __restrict__ out,
+                           int64_t batch, int ntau, int nf) {
+  extern __shared__ double2 sT[];
+  for (int i = threadIdx.x; i < nf * ntau; i += blockDim.x) sT[i] = T[i];
+  __syncthreads();
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  for (int j0 = 0; j0 < nf; j0 += JB) {
+    double2 acc[JB];
+#pragma unroll
+    for (int q = 0; q < JB; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int i = 0; i < ntau; ++i) {
+      const double2 x = in[(size_t)i * batch + b];
+#pragma unroll
+      for (int q = 0; q < JB; ++q) {
+        if (j0 + q < nf) {
+          const double2 t = sT[(j0 + q) * ntau + i];
+          acc[q].x = fma(t.x, x.x, fma(-t.y, x.y, acc[q].x));
+          acc[q].y = fma(t.x, x.y, fma(t.y, x.x, acc[q].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < JB; ++q)
+      if (j0 + q < nf) out[(size_t)(j0 + q) * batch + b] = acc[q];
+  }
+}
+
+// BOSE i nu -> tau of a Hermitian-matrix function W[j][I][J]:
+// ghat = (W_IJ + W_JI)/2 (transform of Re W(tau)), hhat = (W_IJ - W_JI)/(2i) (of Im W(tau));
+// Re W(tau_i) = sum_j A_ij Re ghat_j + B_ij Im ghat_j, Im W(tau_i) likewise with hhat.
+__global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W, double2* __restrict__ out,
+                           int m, int ntau, int nf) {
+  extern __shared__ double sTb[];
+  for (int i = threadIdx.x; i < ntau * 2 * nf; i += blockDim.x) sTb[i] = Tb[i];
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t mm = (int64_t)m * m;
+  if (e >= mm) return;
+  const int I = (int)(e / m), J = (int)(e % m);
+  const int64_t et = (int64_t)J * m + I;
+  for (int i0 = 0; i0 < ntau; i0 += 8) {
+    double gr[8], gi[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) gr[q] = gi[q] = 0.0;
+    for (int j = 0; j < nf; ++j) {
+      const double2 a = W[(size_t)j * mm + e], b = W[(size_t)j * mm + et];
+      const double ghr = 0.5 * (a.x + b.x), ghi = 0.5 * (a.y + b.y);
+      // (a - b)/(2i) = (a.y - b.y)/2 - i (a.x - b.x)/2
+      const double hhr = 0.5 * (a.y - b.y), hhi = -0.5 * (a.x - b.x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (i0 + q < ntau) {
+          const double A = sTb[(i0 + q) * 2 * nf + j], B = sTb[(i0 + q) * 2 * nf + nf + j];
+          gr[q] = fma(A, ghr, fma(B, ghi, gr[q]));
+          gi[q] = fma(A, hhr, fma(B, hhi, gi[q]));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (i0 + q < ntau) out[(size_t)(i0 + q) * mm + e] = make_double2(gr[q], gi[q]);
+  }
+}
+
+// FERMI tau -> i w of real rows: out[b][j] = sum_i T[j][i] in[b][i]; one thread per (b, j).
+__global__ void k_fermi_fwd(const double2* __restrict__ T, const double* __restrict__ in, double2* __restrict__ out,
+                            int64_t batch, int ntau, int nf) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= batch * nf) return;
+  const int64_t b = e / nf;
+  const int j = (int)(e % nf);
+  double ar = 0.0, ai = 0.0;
+  const double* x = in + (size_t)b * ntau;
+  const double2* t = T + (size_t)j * ntau;
+  for (int i = 0; i < ntau; ++i) {
+    const double xv = x[i];
+    const double2 tv = t[i];
+    ar = fma(tv.x, xv, ar);
+    ai = fma(tv.y, xv, ai);
+  }
+  out[e] = make_double2(ar, ai);
+}
+
+// FERMI i w -> tau of a real function: out[b][i] = sum_j A_ij Re in[b][j] + B_ij Im in[b][j].
+__global__ void k_fermi_bwd(const double* __restrict__ Tb, const double2* __restrict__ in, double* __restrict__ out,
+                            int64_t batch, int ntau, int nf) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= batch * ntau) return;
+  const int64_t b = e / ntau;
+  const int i = (int)(e % ntau);
+  const double* A = Tb + (size_t)i * 2 * nf;
+  const double2* x = in + (size_t)b * nf;
+  double s = 0.0;
+  for (int j = 0; j < nf; ++j) {
+    const double2 v = x[j];
+    s = fma(A[j], v.x, fma(A[nf + j], v.y, s));
+  }
+  out[e] = s;
+}
+
+gw_status launch_transform(gw_ctx* c, int stat, int dir, int64_t batch, const double* in, double* out) {
+  const int nt = c->ntau;
+  if (stat == GW_BOSE && dir == GW_TAU_TO_IW) {
+    const size_t sm = sizeof(double2) * c->nnu * nt;
+    const int64_t blocks = (batch + 127) / 128;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bose_fwd<8><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd, (const double2*)in,
+                                                           (double2*)out, batch, nt, c->nnu);
+    return check_launch(c, "bose_fwd");
+  }
+  if (stat == GW_BOSE && dir == GW_IW_TO_TAU) {
+    const int m = (int)batch;
+    const size_t sm = sizeof(double) * nt * 2 * c->nnu;
+    const int64_t mm = (int64_t)m * m;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bose_bwd<<<(unsigned)((mm + 127) / 128), 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m,
+                                                                      nt, c->nnu);
+    return check_launch(c, "bose_bwd");
+  }
+  if (stat == GW_FERMI && (dir == GW_TAU_TO_IW || dir == GW_TAU_TO_IW_CONT)) {
+    const int nf = dir == GW_TAU_TO_IW ? c->nw : c->ncont;
+    const double* T = dir == GW_TAU_TO_IW ? c->d_Ffwd : c->d_Fcont;
+    const int64_t n = batch * nf;
+    k_fermi_fwd<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>((const double2*)T, in, (double2*)out, batch, nt,
+                                                                    nf);
+    return check_launch(c, "fermi_fwd");
+  }
+  if (stat == GW_FERMI && dir == GW_IW_TO_TAU) {
+    const int64_t n = batch * nt;
+    k_fermi_bwd<<<(unsigned)((n + 127) / 128), 128, 0, c->stream>>>(c->d_Fbwd, (const double2*)in, out, batch, nt,
+                                                                    c->nw);
+    return check_launch(c, "fermi_bwd");
+  }
+  return set_err(c, GW_EINVAL, "gw_tau_to_freq: unsupported stat/dir");
+}
+
+// ----------------------------------------------------------------------------
+// Exchange self-energy, product-basis form of Eq. (sigx) with diagonal v:
+// Sigx_n(k) += -1/(Omega Nk) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2. One block per k,
+// threads over n; deterministic (no atomics).
+// ----------------------------------------------------------------------------
+__global__ void k_sigx(const double2* __restrict__ M, const double* __restrict__ v, const int* __restrict__ kmq,
+                       const double* __restrict__ occ, int nk, int ni, int nb, double pref, double* __restrict__ Sx) {
+  const int k = blockIdx.x;
+  const double2* Mk = M + (size_t)k * ni * nb * nb;
+  const int km = kmq[k];
+  for (int n = threadIdx.x; n < nb; n += blockDim.x) {
+    double s = 0.0;
+    for (int j = 0; j < nb; ++j) {
+      const double f = occ[(size_t)km * nb + j];
+      double t = 0.0;
+      for (int I = 0; I < ni; ++I) {
+        const double2 m = Mk[((size_t)I * nb + j) * nb + n];
+        t = fma(v[I], m.x * m.x + m.y * m.y, t);
+      }
+      s = fma(f, t, s);
+    }
+    Sx[(size_t)k * nb + n] += pref * s;
+  }
+}
+
+gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx) {
+  const double2* M = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * c->nb * c->nb;
+  k_sigx<<<c->nk, 128, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->d_kmq + (size_t)iq * c->nk, occ, c->nk,
+                                       c->ni, c->nb, -1.0 / (c->omega * c->nk), Sx);
+  return check_launch(c, "sigx");
+}
+
+}  // namespace gwi
+
+using namespace gwi;
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+static bool grid_ok(const gw_grid* g) {
+  if (!g || g->ntau <= 0 || g->ntau > 256 || (g->ntau & 1) || !g->tau || g->npole < 1 || g->npole > g->ntau ||
+      !g->poles || g->nnu < 1 || !g->nu_idx || g->nw < 1 || !g->w_idx || g->ncont < 1 || g->ncont > 512 ||
+      !(g->beta > 0) || 2 * g->nnu < g->npole || 2 * g->nw < g->npole)
+    return false;
+  for (int i = 0; i < g->ntau; ++i) {
+    if (!(g->tau[i] > 0 && g->tau[i] < g->beta)) return false;
+    if (i && !(g->tau[i] > g->tau[i - 1])) return false;
+    if (std::fabs(g->tau[i] + g->tau[g->ntau - 1 - i] - g->beta) > 1e-12 * g->beta) return false;
+  }
+  for (int i = 0; i < g->nnu; ++i)
+    if (g->nu_idx[i] < 0) return false;
+  for (int i = 0; i < g->nw; ++i)
+    if (g->w_idx[i] < 0) return false;
+  return true;
+}
+
+static gw_status upload(gw_ctx* c, double** dst, const std::vector<double>& h) {
+  if (cudaMalloc((void**)dst, sizeof(double) * std::max<size_t>(1, h.size())) != cudaSuccess)
+    return set_err(c, GW_ENOMEM, "cudaMalloc failed");
+  if (!h.empty() && cudaMemcpy(*dst, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_err(c, GW_ECUDA, "cudaMemcpy failed");
+  return GW_OK;
+}
+
+gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int device, void* stream) {
+  if (!out || !g || !s) return GW_EINVAL;
+  *out = nullptr;
+  if (!grid_ok(g)) return GW_EINVAL;
+  if (s->nk < 1 || s->nq < 1 || s->nb < 1 || s->nb > 256 || s->ni < 16 || s->ni > 1024 || (s->ni % 32) || !s->kmq ||
+      !s->v || !(s->omega > 0))
+    return GW_EINVAL;
+  for (int i = 0; i < s->nq * s->nk; ++i)
+    if (s->kmq[i] < 0 || s->kmq[i] >= s->nk) return GW_EINVAL;
+  for (int i = 0; i < s->nq * s->ni; ++i)
+    if (!(s->v[i] > 0)) return GW_EINVAL;
+
+  gw_ctx* c = new gw_ctx();
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return GW_ECUDA;
+  }
+  c->stream = (cudaStream_t)stream;
+  c->beta = g->beta;
+  c->ntau = g->ntau;
+  c->npole = g->npole;
+  c->nnu = g->nnu;
+  c->nw = g->nw;
+  c->ncont = g->ncont;
+  c->tau.assign(g->tau, g->tau + g->ntau);
+  c->poles.assign(g->poles, g->poles + g->npole);
+  c->nu_idx.assign(g->nu_idx, g->nu_idx + g->nnu);
+  c->w_idx.assign(g->w_idx, g->w_idx + g->nw);
+  c->seed = s->seed;
+  c->nk = s->nk;
+  c->nq = s->nq;
+  c->nb = s->nb;
+  c->nocc = s->nocc;
+  c->ni = s->ni;
+  c->omega = s->omega;
+  c->kmq.assign(s->kmq, s->kmq + (size_t)s->nq * s->nk);
+  c->v.assign(s->v, s->v + (size_t)s->nq * s->ni);
+
+  build_transforms(c->tau, c->poles, c->beta, c->nu_idx, c->w_idx, c->ncont, &c->T);
+
+  gw_status st = GW_OK;
+  std::vector<double> sv(c->v.size());
+  for (size_t i = 0; i < sv.size(); ++i) sv[i] = std::sqrt(c->v[i]);
+  if ((st = upload(c, &c->d_v, c->v)) || (st = upload(c, &c->d_sqrtv, sv)) ||
+      (st = upload(c, &c->d_Bfwd, c->T.B_fwd)) || (st = upload(c, &c->d_Ffwd, c->T.F_fwd)) ||
+      (st = upload(c, &c->d_Fcont, c->T.F_cont)) || (st = upload(c, &c->d_Bbwd, c->T.B_bwd)) ||
+      (st = upload(c, &c->d_Fbwd, c->T.F_bwd)) || (st = upload(c, &c->d_Fbwd_beta, c->T.F_bwd_beta))) {
+    gw_destroy(c);
+    return st;
+  }
+  if (cudaMalloc((void**)&c->d_kmq, sizeof(int) * c->kmq.size()) != cudaSuccess) {
+    gw_destroy(c);
+    return GW_ENOMEM;
+  }
+  cudaMemcpy(c->d_kmq, c->kmq.data(), sizeof(int) * c->kmq.size(), cudaMemcpyHostToDevice);
+  if ((st = upload(c, &c->d_tau, c->tau)) != GW_OK) {
+    gw_destroy(c);
+    return st;
+  }
+  if (cudaMalloc((void**)&c->d_widx, sizeof(int) * c->nw) != cudaSuccess) {
+    gw_destroy(c);
+    return GW_ENOMEM;
+  }
+  cudaMemcpy(c->d_widx, c->w_idx.data(), sizeof(int) * c->nw, cudaMemcpyHostToDevice);
+
+  if (s->M) {
+    c->d_M = s->M;
+  } else {
+    const size_t bytes = (size_t)c->nq * c->nk * c->ni * c->nb * c->nb * sizeof(double2);
+    if (cudaMalloc((void**)&c->d_M_own, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      gw_destroy(c);
+      return GW_ENOMEM;
+    }
+    c->d_M = c->d_M_own;
+    if ((st = launch_gen_m(c, c->d_M_own)) != GW_OK) {
+      gw_destroy(c);
+      return st;
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+    gw_destroy(c);
+    return GW_ECUDA;
+  }
+  *out = c;
+  return GW_OK;
+}
+
+gw_status gw_destroy(gw_ctx* c) {
+  if (!c) return GW_EINVAL;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  cudaDeviceSynchronize();
+  double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
+                    c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_b,
+                    c->d_pade};
+  for (double* p : bufs)
+    if (p) cudaFree(p);
+  if (c->d_kmq) cudaFree(c->d_kmq);
+  if (c->d_widx) cudaFree(c->d_widx);
+  if (c->d_tau) cudaFree(c->d_tau);
+  free_mixed(c);
+  delete c;
+  return GW_OK;
+}
+
+gw_status gw_sync(gw_ctx* c) {
+  if (!c) return GW_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return set_err(c, GW_ECUDA, std::string("gw_sync: ") + cudaGetErrorString(e));
+  return GW_OK;
+}
+
+const char* gw_last_error(gw_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+gw_status gw_green_tau(gw_ctx* c, const double* eps, const double* sigx, const double* vxc, const double* sigc_iw,
+                       double* G, double* occ) {
+  if (!c || !eps || !G || !occ) return GW_EINVAL;
+  if (!sigx && !vxc && !sigc_iw) return launch_green0(c, eps, G, occ);
+  return launch_dyson(c, eps, sigx, vxc, sigc_iw, G, occ);
+}
+
+gw_status gw_polarization(gw_ctx* c, int iq, const double* G, gw_prec prec, double* P) {
+  if (!c || !G || !P || iq < 0 || iq >= c->nq) return GW_EINVAL;
+  if (prec == GW_FP64) return launch_pol_fp64(c, iq, G, P);
+  if (prec == GW_FP16X2 || prec == GW_BF16X3) return launch_pol_mixed(c, iq, G, (int)prec, P);
+  return GW_EINVAL;
+}
+
+gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, const double* in, double* out) {
+  if (!c || !in || !out || batch <= 0) return GW_EINVAL;
+  if (stat == GW_BOSE && dir == GW_TAU_TO_IW_CONT) return GW_EINVAL;
+  return launch_transform(c, (int)stat, (int)dir, batch, in, out);
+}
+
+gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W, int* info) {
+  if (!c || !P || !W || !info || iq0 < 0 || nqb < 1 || iq0 + nqb > c->nq) return GW_EINVAL;
+  const size_t need = (size_t)nqb * c->nnu * c->ni * 2 * c->ni * sizeof(double2);
+  if (need > c->aug_bytes) {
+    if (c->d_aug) cudaFree(c->d_aug);
+    c->d_aug = nullptr;
+    c->aug_bytes = 0;
+    if (cudaMalloc((void**)&c->d_aug, need) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, GW_ENOMEM, "gw_screen: workspace");
+    }
+    c->aug_bytes = need;
+  }
+  return launch_screen(c, iq0, nqb, P, W, info, c->d_aug);
+}
+
+gw_status gw_selfenergy(gw_ctx* c, int iq, const double* G, const double* occ, const double* W, gw_prec prec,
+                        double* S, double* Sx) {
+  if (!c || !G || !W || !S || iq < 0 || iq >= c->nq || (Sx && !occ)) return GW_EINVAL;
+  gw_status st;
+  if (prec == GW_FP64)
+    st = launch_sigma_fp64(c, iq, G, W, S);
+  else if (prec == GW_FP16X2 || prec == GW_BF16X3)
+    st = launch_sigma_mixed(c, iq, G, W, (int)prec, S);
+  else
+    return GW_EINVAL;
+  if (st != GW_OK) return st;
+  if (Sx) return launch_sigx(c, iq, occ, Sx);
+  return GW_OK;
+}
+
+gw_status gw_continue(gw_ctx* c, gw_cont_method method, int64_t nprob, const double* sig_iw, const double* eps,
+                      const double* sigx, const double* vxc, int nreal, const double* omega_real, double* sig_real,
+                      double* e_qp, int* info) {
+  if (!c || nprob <= 0 || !sig_iw || !eps || !sigx || !vxc || !e_qp || !info || nreal < 0 ||
+      (nreal > 0 && (!omega_real || !sig_real)))
+    return GW_EINVAL;
+  if (method == GW_CPE && c->cpe_ngrid == 0) return set_err(c, GW_EINVAL, "gw_continue: call gw_cpe_setup first");
+  if (method != GW_PADE && method != GW_CPE) return GW_EINVAL;
+  return launch_continue(c, (int)method, nprob, sig_iw, eps, sigx, vxc, nreal, omega_real, sig_real, e_qp, info);
+}
+
+gw_status gw_copy_m(gw_ctx* c, int iq, int k0, int nkc, double* out) {
+  if (!c || !out || iq < 0 || iq >= c->nq || k0 < 0 || nkc < 1 || k0 + nkc > c->nk) return GW_EINVAL;
+  const size_t per_k = (size_t)c->ni * c->nb * c->nb * sizeof(double2);
+  const char* src = (const char*)c->d_M + ((size_t)iq * c->nk + k0) * per_k;
+  if (cudaMemcpyAsync(out, src, per_k * nkc, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return set_err(c, GW_ECUDA, "gw_copy_m");
+  return GW_OK;
+}
+
+gw_status gw_transform_matrices(const gw_grid* g, double* B_fwd, double* F_fwd, double* F_cont, double* B_bwd,
+                                double* F_bwd) {
+  if (!grid_ok(g)) return GW_EINVAL;
+  gwi::Transforms T;
+  build_transforms(std::vector<double>(g->tau, g->tau + g->ntau), std::vector<double>(g->poles, g->poles + g->npole),
+                   g->beta, std::vector<int>(g->nu_idx, g->nu_idx + g->nnu),
+                   std::vector<int>(g->w_idx, g->w_idx + g->nw), g->ncont, &T);
+  auto cp = [](double* d, const std::vector<double>& s) {
+    if (d) std::memcpy(d, s.data(), sizeof(double) * s.size());
+  };
+  cp(B_fwd, T.B_fwd);
+  cp(F_fwd, T.F_fwd);
+  cp(F_cont, T.F_cont);
+  cp(B_bwd, T.B_bwd);
+  cp(F_bwd, T.F_bwd);
+  return GW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Screened interaction at bosonic Matsubara frequencies (Sec. III.B.3, Eq. tildeW posed in i nu):
+//   Pi = v^1/2 P(i nu) v^1/2,  (1 - Pi) X = Pi,  W~ = W - v = v^1/2 X v^1/2.
+// One thread block per (q, nu) system. The augmented matrix [1 - Pi | Pi] (ni x 2 ni,
+// complex FP64) lives in a global workspace (L2-resident for typical sizes) and is
+// reduced by Gaussian elimination without pivoting, then back-substituted.
+// Elimination without pivoting is safe here: P(i nu) has a negative semidefinite
+// Hermitian part, so 1 - Pi has Hermitian part >= 1 and every leading principal
+// submatrix is nonsingular. A zero pivot is still detected and reported in info.
+#include <cuda_runtime.h>
+
+#include "gw_internal.h"
+
+namespace gwi {
+
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cinv(double2 a) {
+  const double d = a.x * a.x + a.y * a.y;
+  return make_double2(a.x / d, -a.y / d);
+}
+
+__global__ void __launch_bounds__(512) k_screen(const double2* __restrict__ P, const double* __restrict__ sqrtv,
+                                                int nnu, int ni, double2* __restrict__ aug_all,
+                                                double2* __restrict__ W, int* __restrict__ info) {
+  const int sys = blockIdx.x;           // = iqb * nnu + j
+  const int iqb = sys / nnu;
+  const int n2 = 2 * ni;
+  const double* sv = sqrtv + (size_t)iqb * ni;
+  const double2* Ps = P + (size_t)sys * ni * ni;
+  double2* A = aug_all + (size_t)sys * ni * n2;
+  __shared__ int bad;
+  __shared__ double2 s_inv;
+  if (threadIdx.x == 0) bad = 0;
+  // build [1 - Pi | Pi]
+  for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
+    const int I = e / ni, J = e % ni;
+    const double s = sv[I] * sv[J];
+    const double2 p = Ps[e];
+    const double2 pi = make_double2(s * p.x, s * p.y);
+    A[(size_t)I * n2 + J] = make_double2((I == J ? 1.0 : 0.0) - pi.x, -pi.y);
+    A[(size_t)I * n2 + ni + J] = pi;
+  }
+  __syncthreads();
+  // forward elimination
+  for (int kk = 0; kk < ni; ++kk) {
+    if (threadIdx.x == 0) {
+      const double2 pv = A[(size_t)kk * n2 + kk];
+      if (pv.x == 0.0 && pv.y == 0.0) {
+        bad = kk + 1;
+      } else {
+        s_inv = cinv(pv);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const int rows = ni - kk - 1, cols = n2 - kk - 1;
+    const double2 inv = s_inv;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int i = kk + 1 + e / cols, j = kk + 1 + e % cols;
+      const double2 l = cmul(A[(size_t)i * n2 + kk], inv);
+      const double2 u = A[(size_t)kk * n2 + j];
+      double2 a = A[(size_t)i * n2 + j];
+      a.x -= l.x * u.x - l.y * u.y;
+      a.y -= l.x * u.y + l.y * u.x;
+      A[(size_t)i * n2 + j] = a;
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) info[sys] = bad;
+    return;
+  }
+  // back substitution on the right-hand block, in place
+  for (int kk = ni - 1; kk >= 0; --kk) {
+    const double2 inv = cinv(A[(size_t)kk * n2 + kk]);
+    for (int j = threadIdx.x; j < ni; j += blockDim.x) {
+      const double2 x = cmul(A[(size_t)kk * n2 + ni + j], inv);
+      A[(size_t)kk * n2 + ni + j] = x;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kk * ni; e += blockDim.x) {
+      const int i = e / ni, j = e % ni;
+      const double2 l = A[(size_t)i * n2 + kk];
+      const double2 x = A[(size_t)kk * n2 + ni + j];
+      double2 a = A[(size_t)i * n2 + ni + j];
+      a.x -= l.x * x.x - l.y * x.y;
+      a.y -= l.x * x.y + l.y * x.x;
+      A[(size_t)i * n2 + ni + j] = a;
+    }
+    __syncthreads();
+  }
+  double2* Ws = W + (size_t)sys * ni * ni;
+  for (int e = threadIdx.x; e < ni * ni; e += blockDim.x) {
+    const int I = e / ni, J = e % ni;
+    const double s = sv[I] * sv[J];
+    const double2 x = A[(size_t)I * n2 + ni + J];
+    Ws[e] = make_double2(s * x.x, s * x.y);
+  }
+  if (threadIdx.x == 0) info[sys] = 0;
+}
+
+}  // namespace
+
+gw_status launch_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W, int* info, double* aug) {
+  const int nsys = nqb * c->nnu;
+  k_screen<<<nsys, 512, 0, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu, c->ni,
+                                        (double2*)aug, (double2*)W, info);
+  return check_launch(c, "screen");
+}
+
+}  // namespace gwi

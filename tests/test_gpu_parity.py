@@ -1,0 +1,328 @@
+"""GPU parity of every libgw step against the FP64 oracle, called through the C ABI.
+
+Tolerances: the FP64 path is held to 1e-10 relative (max-norm error over the
+max-norm of the oracle result), the bar the work is specified against; most
+steps agree to ~1e-14. Sizes span several tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import gwinputs as gi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gw():
+    from paper_1602_02313_gb300 import build as b
+    b.build()
+    import paper_1602_02313_gb300 as pkg
+    return pkg
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def zeros(shape, dtype="f8"):
+    import torch
+    return torch.zeros(shape, dtype={"f8": torch.float64, "c16": torch.complex128, "i4": torch.int32}[dtype],
+                       device="cuda")
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def small_case(name="c1", **over):
+    cr, gr = gi.make_config(name, **over)
+    return cr, gr
+
+
+def ragged_case():
+    # nk = 3 (3x1x1 mesh), nb = 5, ni = 32, ntau = 8: one tile, ragged band tails
+    cr = gi.make_crystal(77, 3, 5, 2, 32, 30.0, qlist=[1, 2])
+    gr = gi.make_grid(30.0, 8, 8, 8, ncont=24)
+    return cr, gr
+
+
+@pytest.fixture(scope="module")
+def c1(gw):
+    cr, gr = small_case()
+    ctx = gw.GW(gr, cr, omega=1.0)
+    return cr, gr, ctx
+
+
+# ------------------------------------------------------------------ inputs
+def test_matrix_elements_match_generator(gw, c1):
+    cr, gr, ctx = c1
+    out = zeros((cr.nk, cr.ni, cr.nb, cr.nb), "c16")
+    ctx.copy_m(0, 0, cr.nk, out)
+    ctx.sync()
+    ref = gi.m_for_q(cr, 0)
+    assert rel(host(out), ref) < 1e-14
+
+
+# ------------------------------------------------------------------ G
+def test_green0(gw, c1):
+    cr, gr, ctx = c1
+    G = zeros((cr.nk, cr.nb, gr.ntau))
+    occ = zeros((cr.nk, cr.nb))
+    ctx.green_tau(dev(cr.eps), G, occ)
+    ctx.sync()
+    Gr, occr = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    assert np.abs(host(G) - Gr).max() < 1e-15
+    assert np.abs(host(occ) - occr).max() < 1e-15
+
+
+# ------------------------------------------------------------------ P
+@pytest.mark.parametrize("case", ["c1", "ragged"])
+def test_polarization_fp64(gw, case):
+    cr, gr = small_case() if case == "c1" else ragged_case()
+    ctx = gw.GW(gr, cr, omega=1.3)
+    G, _ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    for iq in range(cr.nq):
+        P = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+        ctx.polarization(iq, dev(G), P, gw.GW_FP64)
+        ctx.sync()
+        ref = orc.polarization(gi.m_for_q(cr, iq), G, cr.kmq[iq], omega=1.3)
+        assert rel(host(P), ref) < TOL
+
+
+# ------------------------------------------------------------------ transforms
+@pytest.mark.parametrize("case", ["c1", "ragged"])
+def test_transforms(gw, case):
+    cr, gr = small_case() if case == "c1" else ragged_case()
+    ctx = gw.GW(gr, cr)
+    T = orc.transform_matrices(gr)
+    rng = np.random.default_rng(3)
+    m = 37
+    x = rng.standard_normal((gr.ntau, m, m)) + 1j * rng.standard_normal((gr.ntau, m, m))
+    y = zeros((gr.nnu, m, m), "c16")
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_TAU_TO_IW, m * m, dev(x), y)
+    ctx.sync()
+    assert rel(host(y), np.einsum("ji,iab->jab", T["B_fwd"], x)) < 1e-13
+    W = rng.standard_normal((gr.nnu, m, m)) + 1j * rng.standard_normal((gr.nnu, m, m))
+    Wt = zeros((gr.ntau, m, m), "c16")
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_IW_TO_TAU, m, dev(W), Wt)
+    ctx.sync()
+    assert rel(host(Wt), orc.transforms.apply_bwd_hermitian(T["B_bwd_re"], T["B_bwd_im"], W)) < 1e-13
+    s = rng.standard_normal((29, gr.ntau))
+    for d, key, nf in [(gw.GW_TAU_TO_IW, "F_fwd", gr.nw), (gw.GW_TAU_TO_IW_CONT, "F_cont", gr.ncont)]:
+        o = zeros((29, nf), "c16")
+        ctx.tau_to_freq(gw.GW_FERMI, d, 29, dev(s), o)
+        ctx.sync()
+        assert rel(host(o), orc.transforms.apply_fwd(T[key], s)) < 1e-13
+    f = rng.standard_normal((29, gr.nw)) + 1j * rng.standard_normal((29, gr.nw))
+    o = zeros((29, gr.ntau))
+    ctx.tau_to_freq(gw.GW_FERMI, gw.GW_IW_TO_TAU, 29, dev(f), o)
+    ctx.sync()
+    assert rel(host(o), orc.transforms.apply_bwd_real(T["F_bwd_re"], T["F_bwd_im"], f)) < 1e-13
+
+
+# ------------------------------------------------------------------ screen
+@pytest.mark.parametrize("case", ["c1", "ragged"])
+def test_screen(gw, case):
+    cr, gr = small_case() if case == "c1" else ragged_case()
+    ctx = gw.GW(gr, cr, omega=0.7)
+    P = np.stack([orc.lindhard_iv(gi.m_for_q(cr, iq), cr.eps, cr.kmq[iq], gr.nu_idx, gr.beta, omega=0.7)
+                  for iq in range(cr.nq)])
+    W = zeros(P.shape, "c16")
+    info = zeros((cr.nq, gr.nnu), "i4")
+    ctx.screen(0, cr.nq, dev(P), W, info)
+    ctx.sync()
+    assert np.all(host(info) == 0)
+    for iq in range(cr.nq):
+        assert rel(host(W)[iq], orc.screen(P[iq], cr.v[iq])) < TOL
+
+
+# ------------------------------------------------------------------ self-energy
+@pytest.mark.parametrize("case", ["c1", "ragged"])
+def test_selfenergy_fp64(gw, case):
+    cr, gr = small_case() if case == "c1" else ragged_case()
+    ctx = gw.GW(gr, cr, omega=1.1)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    rng = np.random.default_rng(5)
+    S = zeros((cr.nk, cr.nb, gr.ntau))
+    Sx = zeros((cr.nk, cr.nb))
+    Sref = np.zeros((cr.nk, cr.nb, gr.ntau))
+    Sxref = np.zeros((cr.nk, cr.nb))
+    for iq in range(cr.nq):
+        X = rng.standard_normal((gr.ntau, cr.ni, cr.ni)) + 1j * rng.standard_normal((gr.ntau, cr.ni, cr.ni))
+        W = -(X @ np.conj(np.swapaxes(X, 1, 2))) / cr.ni        # Hermitian, like W~(tau)
+        ctx.selfenergy(iq, dev(G), dev(occ), dev(W), S, Sx, gw.GW_FP64)
+        sc, sx, im = orc.selfenergy(gi.m_for_q(cr, iq), G, W, cr.v[iq], cr.kmq[iq], occ, omega=1.1)
+        assert im < 1e-12 * np.abs(sc).max()
+        Sref += sc
+        Sxref += sx
+    ctx.sync()
+    assert rel(host(S), Sref) < TOL
+    assert rel(host(Sx), Sxref) < 1e-13
+
+
+# ------------------------------------------------------------------ Dyson
+def test_dyson(gw, c1):
+    cr, gr, ctx = c1
+    rng = np.random.default_rng(8)
+    sx = rng.uniform(-3, -1, (cr.nk, cr.nb))
+    vxc = sx + rng.uniform(-0.01, 0.01, (cr.nk, cr.nb))
+    w = (2 * gr.w_idx + 1) * np.pi / gr.beta
+    sig = (0.02 / (1j * w[None, None, :] - rng.uniform(-2, 2, (cr.nk, cr.nb, 1))))
+    G = zeros((cr.nk, cr.nb, gr.ntau))
+    occ = zeros((cr.nk, cr.nb))
+    ctx.green_tau(dev(cr.eps), G, occ, dev(sx), dev(vxc), dev(sig))
+    ctx.sync()
+    Gr, occr = orc.dyson_iw(cr.eps, sx, vxc, sig, gr)
+    assert rel(host(G), Gr) < 1e-13
+    assert np.abs(host(occ) - occr).max() < 1e-13
+
+
+# ------------------------------------------------------------------ continuation
+def _model_sigma(nprob, ncont, beta, seed=0):
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-1.5, 1.5, (nprob, 3))
+    r = rng.uniform(0.01, 0.05, (nprob, 3))
+    z = 1j * (2 * np.arange(ncont) + 1) * np.pi / beta
+    return (r[:, None, :] / (z[None, :, None] - e[:, None, :])).sum(-1), e, r
+
+
+def test_pade_and_qp(gw, c1):
+    cr, gr, ctx = c1
+    nprob = 20
+    sig, _, _ = _model_sigma(nprob, gr.ncont, gr.beta)
+    eps = np.linspace(-0.9, 0.9, nprob)
+    sx = np.full(nprob, -2.0)
+    vxc = np.full(nprob, -2.05)
+    wr = np.linspace(-2, 2, 11)
+    sr = zeros((nprob, 11), "c16")
+    eq = zeros(nprob)
+    info = zeros(nprob, "i4")
+    ctx.continue_(gw.GW_PADE, dev(sig), dev(eps), dev(sx), dev(vxc), dev(wr), sr, eq, info)
+    ctx.sync()
+    npade = min(gr.ncont, 64)
+    z = 1j * (2 * np.arange(npade) + 1) * np.pi / gr.beta
+    for p in range(nprob):
+        a = orc.pade_coeffs(z, sig[p, :npade])
+        ref = orc.pade_eval(a, z, wr + 1j * orc.ETA)
+        assert np.abs(host(sr)[p] - ref).max() < 1e-8 * np.abs(ref).max()
+        E, _, ok = orc.qp_solve(eps[p], sx[p], vxc[p], orc.pade_resig(a, z))
+        assert abs(host(eq)[p] - E) < 1e-9
+        assert (host(info)[p] == 0) == ok
+
+
+def test_cpe_and_qp(gw, c1):
+    cr, gr, ctx = c1
+    nprob = 12
+    sig, _, _ = _model_sigma(nprob, gr.ncont, gr.beta, seed=1)
+    x = orc.cpe_grid(64, 0.02, 20.0)
+    ridge = 1e-5
+    ctx.cpe_setup(x, ridge)
+    eps = np.linspace(-0.9, 0.9, nprob)
+    sx = np.full(nprob, -2.0)
+    vxc = np.full(nprob, -2.0)
+    wr = np.linspace(-2, 2, 7)
+    sr = zeros((nprob, 7), "c16")
+    eq = zeros(nprob)
+    info = zeros(nprob, "i4")
+    ctx.continue_(gw.GW_CPE, dev(sig), dev(eps), dev(sx), dev(vxc), dev(wr), sr, eq, info)
+    b = zeros((nprob, 64))
+    ctx.cpe_coeffs(b)
+    ctx.sync()
+    w = (2 * np.arange(gr.ncont) + 1) * np.pi / gr.beta
+    K = orc.cpe_kernel(x, 1j * w)
+    for p in range(nprob):
+        bref, _ = orc.cpe_fit(w, sig[p], x, ridge=ridge)
+        bg = host(b)[p]
+        assert np.all(bg >= 0)
+        # the regularised NNLS minimiser is unique: compare the fitted Matsubara values
+        fit_g, fit_r = K @ bg, K @ bref
+        assert np.abs(fit_g - fit_r).max() < 1e-6 * np.abs(sig[p]).max()
+        assert np.abs(bg - bref).max() < 1e-4 * max(np.abs(bref).max(), 1e-12)
+        E, _, ok = orc.qp_solve(eps[p], sx[p], vxc[p], orc.cpe_resig(bg, x))
+        assert abs(host(eq)[p] - E) < 1e-9
+
+
+# ------------------------------------------------------------------ whole chain (c1)
+def test_g0w0_chain_c1(gw, c1):
+    """G0 -> P -> P(i nu) -> W~(i nu) -> W~(tau) -> Sigma(tau) -> Sigma(i w) -> Dyson G,
+    every step on the GPU, against the same chain in the oracle."""
+    cr, gr, ctx = c1
+    import torch
+    G = zeros((cr.nk, cr.nb, gr.ntau))
+    occ = zeros((cr.nk, cr.nb))
+    ctx.green_tau(dev(cr.eps), G, occ)
+    S = zeros((cr.nk, cr.nb, gr.ntau))
+    Sx = zeros((cr.nk, cr.nb))
+    P = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    Piv = zeros((gr.nnu, cr.ni, cr.ni), "c16")
+    Wiv = zeros((gr.nnu, cr.ni, cr.ni), "c16")
+    Wt = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    info = zeros((1, gr.nnu), "i4")
+    ctx.polarization(0, G, P, gw.GW_FP64)
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_TAU_TO_IW, cr.ni * cr.ni, P, Piv)
+    ctx.screen(0, 1, Piv, Wiv, info)
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_IW_TO_TAU, cr.ni, Wiv, Wt)
+    ctx.selfenergy(0, G, occ, Wt, S, Sx, gw.GW_FP64)
+    Siw = zeros((cr.nk, cr.nb, gr.nw), "c16")
+    ctx.tau_to_freq(gw.GW_FERMI, gw.GW_TAU_TO_IW, cr.nk * cr.nb, S, Siw)
+    G1 = zeros((cr.nk, cr.nb, gr.ntau))
+    occ1 = zeros((cr.nk, cr.nb))
+    ctx.green_tau(dev(cr.eps), G1, occ1, Sx, Sx.clone(), Siw)
+    ctx.sync()
+    # oracle
+    M = gi.m_for_q(cr, 0)
+    G0, f0 = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    Pr = orc.polarization(M, G0, cr.kmq[0])
+    Wr = orc.screen(orc.tau_to_nu(Pr, gr), cr.v[0])
+    Wtr = orc.nu_to_tau(Wr, gr)
+    Sr, Sxr, _ = orc.selfenergy(M, G0, Wtr, cr.v[0], cr.kmq[0], f0)
+    Siwr = orc.sigma_tau_to_iw(Sr, gr)
+    G1r, occ1r = orc.dyson_iw(cr.eps, Sxr, Sxr, Siwr, gr)
+    assert np.all(host(info) == 0)
+    assert rel(host(P), Pr) < TOL
+    assert rel(host(Wiv), Wr) < TOL
+    assert rel(host(Wt), Wtr) < TOL
+    assert rel(host(S), Sr) < TOL
+    assert rel(host(Sx), Sxr) < TOL
+    assert rel(host(Siw), Siwr) < TOL
+    assert rel(host(G1), G1r) < TOL
+    assert np.abs(host(occ1) - occ1r).max() < TOL
+
+
+# ------------------------------------------------------------------ full size (c2), sampled
+def test_c2_full_size_sampled(gw):
+    """The bench workload's sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): FP64 P of
+    one q at sampled tau, and Sigma^c at sampled (k, tau), against the oracle."""
+    cr, gr = gi.make_config("c2", qlist=[5])
+    ctx = gw.GW(gr, cr)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    P = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    ctx.polarization(0, dev(G), P, gw.GW_FP64)
+    ctx.sync()
+    its = [0, 17, 47]
+    M = gi.m_for_q(cr, 0)
+    Pr = orc.polarization(M, G, cr.kmq[0], its=its)
+    Pg = host(P)[its]
+    assert rel(Pg, Pr) < TOL
+    # Hermitian and negative semidefinite at every sampled tau
+    for P_ in Pg:
+        assert np.linalg.eigvalsh(0.5 * (P_ + P_.conj().T)).max() < 1e-12 * np.abs(P_).max()
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((gr.ntau, cr.ni, 8)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 8))
+    W = -(X @ np.conj(np.swapaxes(X, 1, 2))) / 8
+    S = zeros((cr.nk, cr.nb, gr.ntau))
+    ctx.selfenergy(0, dev(G), dev(occ), dev(W), S, None, gw.GW_FP64)
+    ctx.sync()
+    ks = [0, 41]
+    Sr, _, _ = orc.selfenergy(M[ks], G, W, cr.v[0], cr.kmq[0], occ, ks=ks, its=its)
+    Sg = host(S)
+    for k in ks:
+        assert rel(Sg[k][:, its], Sr[k][:, its]) < TOL
