@@ -1,0 +1,339 @@
+"""Benchmark of one GW iteration (G0W0 pass) of the Matsubara-time GW hot path.
+
+Workload: synthetic crystal shaped like the paper's (Nk = 64 on a 4x4x4 grid, q on
+the same grid, Nb = 64 with 32 occupied, NI = 256, Ntau = 48 Gauss-Legendre-in-log
+nodes, 48 bosonic / fermionic Matsubara nodes, beta = 200 / Ha). One step = every
+row of the hot path over all 64 q: G0, P(tau) (tensor cores), tau -> i nu, screening,
+i nu -> tau, Sigma^c(tau) + Sigma^x (tensor cores), Sigma(i w) on the sparse and the
+continuation sets, Dyson update, Pade continuation and QP energies.
+
+metric / value: P + Sigma contraction throughput over the whole iteration, in
+algorithmic TFLOP/s (8 real flops per complex multiply-add, Hermitian half of P);
+ms_per_step is the GW iteration time.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp16x2|fp64]
+       python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+Multi-GPU (torchrun, one rank per GPU): the q points are split over the ranks, each
+rank computes its Sigma contributions and one all-reduce sums Sigma^c(tau), Sigma^x.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GW iteration time & P/Sigma contraction TFLOP/s, mixed vs FP64, at <=1 meV gap error"
+FALLBACK_TENSOR_SUSTAINED = 1700.0   # TFLOP/s, profiling-recipe fallback (no MEASURED_PEAKS.json)
+FALLBACK_TENSOR_BURST = 1900.0
+FALLBACK_HBM = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return {"tensor_sustained": float(d.get("bf16_tflops_sustained", d.get("bf16_tflops"))),
+                    "tensor_burst": float(d.get("bf16_tflops")), "hbm": float(d.get("hbm_gbs")),
+                    "source": "measured (MEASURED_PEAKS.json)"}
+        except Exception:
+            pass
+    return {"tensor_sustained": FALLBACK_TENSOR_SUSTAINED, "tensor_burst": FALLBACK_TENSOR_BURST,
+            "hbm": FALLBACK_HBM, "source": "fallback (profiling recipe; MEASURED_PEAKS.json absent)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken
+    on the current source of the kernel; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1602_02313_gb300", "csrc", "tc_mixed.cu")
+    try:
+        d = json.load(open(p)).get(kernel)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d and d.get("src_sha") == sha:
+            return d["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def cpu_sample(cr, gr, omega, its=(0, 11, 23, 35), ks=(0, 9, 17, 26, 33, 41, 50, 60)):
+    """The FP64 oracle on a bounded sample of the workload: P of one q at len(its) tau
+    values (all k), and Sigma^c of one q at len(ks) k points x len(its) tau values.
+    Returns (flops, seconds, description); the M tensor of the q is generated before timing."""
+    import gwinputs as gi
+    import oracle as orc
+    M = gi.m_for_q(cr, 0)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((gr.ntau, cr.ni, 8)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 8))
+    W = -(X @ np.conj(np.swapaxes(X, 1, 2)))
+    t0 = time.perf_counter()
+    orc.polarization(M, G, cr.kmq[0], omega, its=list(its))
+    orc.selfenergy(M[list(ks)], G, W, cr.v[0], cr.kmq[0], occ, omega, ks=list(ks), its=list(its))
+    dt = time.perf_counter() - t0
+    from paper_1602_02313_gb300.driver import contraction_flops
+    fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, 1)
+    flops = fp * len(its) + fs / cr.nk * len(ks) * len(its)
+    desc = (f"oracle P of 1 q at {len(its)} tau (all {cr.nk} k) + Sigma^c of 1 q at {len(ks)} k x {len(its)} tau, "
+            f"numpy/BLAS FP64")
+    return flops, dt, desc
+
+
+def run_reference(args, cfg):
+    import gwinputs as gi
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cr, gr = gi.make_config(cfg)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        cpu_sample(cr, gr, args.omega)
+    tot_f, tot_t = 0.0, 0.0
+    for _ in range(args.steps):
+        f, t, desc = cpu_sample(cr, gr, args.omega)
+        tot_f += f
+        tot_t += t
+    value = tot_f / tot_t / 1e12
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(cfg, args, "oracle"),
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def _config(cfg, args, prec):
+    import gwinputs as gi
+    c = gi.CONFIGS[cfg]
+    return {"workload": f"synthetic crystal {cfg}: Nk={c['nk']} (q on the same grid), Nb={c['nb']} "
+                        f"({c['nocc']} occ), NI={c['ni']}, Ntau={c['ntau']}, Nnu=Nw={c['nnu']}, beta={c['beta']}",
+            "precision": prec, "omega": args.omega, "parallelism": f"q-split over {args.gpus} GPU(s)",
+            "l2": "inputs larger than L2 (M tensor 69 GB, P/W per q 50 MB each)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
+    ap.add_argument("--prec", default="fp16x2", choices=["fp16x2", "fp64"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--omega", type=float, default=1.0)
+    ap.add_argument("--nq", type=int, default=0, help="limit q points (exploration only; not a bench line)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.config)
+
+    import torch
+    import torch.distributed as dist
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300.driver import Chain, contraction_flops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1602_02313_gb300 import build as b
+    if rank == 0:
+        b.build()
+    if world > 1:
+        dist.barrier()
+    prec = gw.PREC[args.prec]
+    full, gr = gi.make_config(args.config)
+    nq = full.nq if args.nq <= 0 else min(args.nq, full.nq)
+    per = (nq + world - 1) // world
+    q0 = min(rank * per, nq)
+    cnt = max(0, min(per, nq - q0))
+    cr = gi.subset_q(full, q0, max(cnt, 1))
+    stream = torch.cuda.current_stream()
+    ctx = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)
+    eps = torch.from_numpy(cr.eps).cuda()
+    chain = Chain(ctx, eps, prec=prec, qb=8, iqs=list(range(cnt)))
+    fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, gr.ntau)
+    flops_step = (fp + fs) * nq
+
+    def one_step():
+        chain.start_g0()
+        chain.sigma()
+        if world > 1:
+            dist.all_reduce(chain.S)
+            dist.all_reduce(chain.Sx)
+        chain.finish()
+
+    for _ in range(args.warmup):
+        one_step()
+    chain.check()
+    # ---------------------------------------------------------------- timed region
+    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if "CUDA_VISIBLE_DEVICES" in os.environ else local
+    sampler = ClockSampler(smi_index)
+    chain.timers = {}
+    launches0 = ctx.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = ctx.launch_count() - launches0
+    chain.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = flops_step / (ms * 1e-3) / 1e12
+    # per-call timings of the two contractions
+    kt = {}
+    for key, evs in chain.timers.items():
+        d = [a.elapsed_time(b_) for a, b_ in evs]
+        kt[key] = float(np.mean(d))
+    chain.timers = None
+    per_launch_flops = {"polarization": fp, "selfenergy": fs}
+    dom = max(kt, key=lambda k: kt[k] * len(chain.iqs)) if kt else "selfenergy"
+    peaks = _peaks()
+    achieved = per_launch_flops[dom] / (kt[dom] * 1e-3) / 1e12 if dom in kt else None
+    kname = {"polarization": "k_pol_tc", "selfenergy": "k_sig_tc"}[dom] if prec != gw.GW_FP64 else dom
+    peak = peaks["tensor_sustained"]
+    roof = {"bound": "tensor" if prec != gw.GW_FP64 else "alu", "kernel": kname + " (whole gw_" + dom + " call)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": _traffic(kname),
+            "peak_source": peaks["source"] + ", sustained bf16/fp16 dense",
+            "per_call_ms": kt, "flops_per_call": per_launch_flops}
+
+    # ---------------------------------------------------------------- end to end through the public API
+    e2e = None
+    if args.e2e_steps > 0:
+        eps_h = torch.from_numpy(cr.eps).pin_memory()
+        out_h = torch.empty(cr.nk * cr.nb, dtype=torch.float64).pin_memory()
+        sx_h = torch.empty(cr.nk * cr.nb, dtype=torch.float64).pin_memory()
+        ctx.close()
+        del chain
+        torch.cuda.empty_cache()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            c2 = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)   # M generated from the seed
+            eps_d = eps_h.to("cuda", non_blocking=True)
+            ch = Chain(c2, eps_d, prec=prec, qb=8, iqs=list(range(cnt)))
+            ch.start_g0()
+            ch.sigma()
+            if world > 1:
+                dist.all_reduce(ch.S)
+                dist.all_reduce(ch.Sx)
+            ch.finish()
+            out_h.copy_(ch.eqp, non_blocking=True)
+            sx_h.copy_(ch.Sx.reshape(-1), non_blocking=True)
+            torch.cuda.synchronize()
+            c2.close()
+            del ch
+        dt = (time.perf_counter() - t0) / args.e2e_steps
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": flops_step / dt / 1e12, "unit": "TFLOP/s", "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(eps_h.numel() * 8 + cr.v.nbytes + cr.kmq.nbytes + gr.tau.nbytes),
+               "d2h_bytes_per_step": int(out_h.numel() * 8 + sx_h.numel() * 8),
+               "includes": "gw_create (transform matrices, M generated on the GPU from the seed), H2D of eps, "
+                           "the iteration, D2H of QP energies and Sigma^x, gw_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        f, t, desc = cpu_sample(full, gr, args.omega)
+        cpu = {"value": f / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+               "vs_baseline": None, "dtype": {"fp16x2": "fp16x2 split (fp32 accum) + f64",
+                                              "fp64": "f64"}[args.prec],
+               "data": "synthetic", "config": _config(args.config, args, args.prec) | {"nq": nq},
+               "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "e2e": e2e,
+               "cpu_baseline": cpu}
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

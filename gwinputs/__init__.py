@@ -210,6 +210,13 @@ def make_crystal(seed, nk, nb, nocc, ni, beta, nq=None, qlist=None):
                    qidx=np.array(qlist, np.int32), mesh=mesh)
 
 
+def subset_q(cr: Crystal, start: int, count: int) -> Crystal:
+    """The q points start .. start+count-1 of a crystal (same eps, v rows and k - q rows);
+    the matrix-element counter of q stays its global position, passed as q0."""
+    return dataclasses.replace(cr, nq=count, v=cr.v[start:start + count].copy(),
+                               kmq=cr.kmq[start:start + count].copy(), qidx=cr.qidx[start:start + count].copy())
+
+
 def m_for_q(cr: Crystal, iq: int, ks=None):
     """M^I_ab(k, q) for the iq-th q and the listed k: complex [len(ks), ni, nb, nb].
 

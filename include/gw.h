@@ -85,8 +85,11 @@ typedef struct {
   const int* kmq;         /* host [nq][nk]: index of k - q */
   const double* v;        /* host [nq][ni]: diagonal Coulomb v_I(q) > 0 */
   const double* M;        /* device cplx [nq][nk][ni][nb][nb], or NULL: libgw generates M
-                             from seed (Philox4x32-10, counter = flat index of (q,k,I,a,b),
-                             Box-Muller, E|M|^2 = 1/nb) and keeps it in its own HBM buffer */
+                             from seed (Philox4x32-10, counter = flat index of
+                             (q0 + iq, k, I, a, b), Box-Muller, E|M|^2 = 1/nb) and keeps it
+                             in its own HBM buffer */
+  int q0;                 /* global index of this context's first q (for the generator
+                             counter; 0 unless the q points are split over several contexts) */
 } gw_system;
 
 /* Create a context on `device`, ordered on the cudaStream_t `stream` (NULL =
@@ -173,6 +176,9 @@ gw_status gw_cpe_coeffs(gw_ctx* ctx, double* b);
 /* Matrix elements the context uses (for inspection and tests): copies
  * M[iq][k][:][:][:] for k in [k0, k0 + nk_copy) into out cplx [nk_copy][ni][nb][nb]. */
 gw_status gw_copy_m(gw_ctx* ctx, int iq, int k0, int nk_copy, double* out);
+
+/* Number of kernels libgw has launched on this context since gw_create (host counter). */
+int64_t gw_launch_count(gw_ctx* ctx);
 
 /* Host-only (no GPU needed): the transform matrices gw_create builds for `grid`,
  * written to host arrays (NULL entries skipped):

@@ -149,7 +149,7 @@ def selfenergy(M, G, W_tau, v, kmq, occ, omega=1.0, ks=None, its=None):
     for m_, k in enumerate(ks):
         A = M[m_].reshape(ni, nb * nb)           # column (a, n)
         for i in its:
-            d = np.einsum("Ip,IJ,Jp->p", A.conj(), W_tau[i], A).reshape(nb, nb)  # [a, n]
+            d = (A.conj() * (W_tau[i] @ A)).sum(0).reshape(nb, nb)  # a^H W a per column (a, n)
             sc[k, :, i] = -(G[kmq[k], :, i][:, None] * d).sum(0) / (omega * nk)
         vm = (np.asarray(v)[:, None] * np.abs(A) ** 2).sum(0).reshape(nb, nb)
         sx[k] = -(occ[kmq[k]][:, None] * vm).sum(0) / (omega * nk)

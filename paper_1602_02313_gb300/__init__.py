@@ -32,7 +32,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 # Every symbol declared in include/gw.h.
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
-           "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices"]
+           "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count"]
 
 
 class GwError(RuntimeError):
@@ -50,7 +50,7 @@ class _System(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("nk", ctypes.c_int), ("nq", ctypes.c_int), ("nb", ctypes.c_int),
                 ("nocc", ctypes.c_int), ("ni", ctypes.c_int), ("omega", ctypes.c_double),
                 ("kmq", ctypes.POINTER(ctypes.c_int)), ("v", ctypes.POINTER(ctypes.c_double)),
-                ("M", ctypes.c_void_p)]
+                ("M", ctypes.c_void_p), ("q0", ctypes.c_int)]
 
 
 def _grid_struct(grid, keep):
@@ -105,11 +105,12 @@ def load_library(path=LIB_PATH):
         "gw_cpe_coeffs": [vp, vp],
         "gw_copy_m": [vp, i32, i32, i32, vp],
         "gw_transform_matrices": [ctypes.POINTER(_Grid), vp, vp, vp, vp, vp],
+        "gw_launch_count": [vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = ctypes.c_char_p if name == "gw_last_error" else ctypes.c_int
+        f.restype = {"gw_last_error": ctypes.c_char_p, "gw_launch_count": ctypes.c_int64}.get(name, ctypes.c_int)
     return lib
 
 
@@ -143,7 +144,7 @@ class GW:
     omega: unit-cell volume in 1/(Omega N_k).
     """
 
-    def __init__(self, grid, crystal, omega=1.0, device=0, stream=None, M=None):
+    def __init__(self, grid, crystal, omega=1.0, device=0, stream=None, M=None, q0=0):
         import torch
         self.lib = lib()
         self.device = device
@@ -158,7 +159,7 @@ class GW:
         g = _grid_struct(grid, self._h)
         s = _System(int(crystal.seed), crystal.nk, crystal.nq, crystal.nb, crystal.nocc, crystal.ni, self.omega,
                     self._h["kmq"].ctypes.data_as(ip), self._h["v"].ctypes.data_as(dp),
-                    None if M is None else ctypes.c_void_p(M.data_ptr()))
+                    None if M is None else ctypes.c_void_p(M.data_ptr()), int(q0))
         self._M = M
         h = ctypes.c_void_p()
         with torch.cuda.device(device):
@@ -184,6 +185,9 @@ class GW:
             self.close()
         except Exception:
             pass
+
+    def launch_count(self):
+        return int(self.lib.gw_launch_count(self.h))
 
     def sync(self):
         self._check(self.lib.gw_sync(self.h), "gw_sync")

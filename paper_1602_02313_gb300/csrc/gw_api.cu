@@ -18,6 +18,7 @@ gw_status set_err(gw_ctx* c, gw_status s, const std::string& msg) {
 }
 
 gw_status check_launch(gw_ctx* c, const char* what) {
+  if (c) ++c->launches;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(c, GW_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
   return GW_OK;
@@ -45,10 +46,11 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
   }
 }
 
-__global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t seed, double scale) {
+__global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t off, uint64_t seed, double scale) {
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t c0 = (uint32_t)idx, c1 = (uint32_t)(idx >> 32), c2 = 0x4Du, c3 = 0u;
+    const uint64_t ctr = idx + off;
+    uint32_t c0 = (uint32_t)ctr, c1 = (uint32_t)(ctr >> 32), c2 = 0x4Du, c3 = 0u;
     philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint64_t m1 = ((uint64_t)c0 << 21) | (c1 >> 11);
     const uint64_t m2 = ((uint64_t)c2 << 21) | (c3 >> 11);
@@ -63,8 +65,9 @@ __global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t seed, doub
 }
 
 gw_status launch_gen_m(gw_ctx* c, double* M) {
-  const uint64_t n = (uint64_t)c->nq * c->nk * c->ni * c->nb * c->nb;
-  k_gen_m<<<152 * 8, 256, 0, c->stream>>>((double2*)M, n, c->seed, std::sqrt(0.5 / c->nb));
+  const uint64_t per_q = (uint64_t)c->nk * c->ni * c->nb * c->nb;
+  const uint64_t n = (uint64_t)c->nq * per_q;
+  k_gen_m<<<152 * 8, 256, 0, c->stream>>>((double2*)M, n, (uint64_t)c->q0 * per_q, c->seed, std::sqrt(0.5 / c->nb));
   return check_launch(c, "gen_m");
 }
 
@@ -359,7 +362,7 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
   if (!out || !g || !s) return GW_EINVAL;
   *out = nullptr;
   if (!grid_ok(g)) return GW_EINVAL;
-  if (s->nk < 1 || s->nq < 1 || s->nb < 1 || s->nb > 256 || s->ni < 16 || s->ni > 1024 || (s->ni % 32) || !s->kmq ||
+  if (s->q0 < 0 || s->nk < 1 || s->nq < 1 || s->nb < 1 || s->nb > 256 || s->ni < 16 || s->ni > 1024 || (s->ni % 32) || !s->kmq ||
       !s->v || !(s->omega > 0))
     return GW_EINVAL;
   for (int i = 0; i < s->nq * s->nk; ++i)
@@ -385,6 +388,7 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
   c->nu_idx.assign(g->nu_idx, g->nu_idx + g->nnu);
   c->w_idx.assign(g->w_idx, g->w_idx + g->nw);
   c->seed = s->seed;
+  c->q0 = s->q0;
   c->nk = s->nk;
   c->nq = s->nq;
   c->nb = s->nb;
@@ -470,6 +474,8 @@ gw_status gw_sync(gw_ctx* c) {
 }
 
 const char* gw_last_error(gw_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int64_t gw_launch_count(gw_ctx* c) { return c ? c->launches : -1; }
 
 gw_status gw_green_tau(gw_ctx* c, const double* eps, const double* sigx, const double* vxc, const double* sigc_iw,
                        double* G, double* occ) {

@@ -53,6 +53,8 @@ struct gw_ctx {
   gwi::Transforms T;
   // system
   uint64_t seed = 0;
+  int q0 = 0;
+  int64_t launches = 0;
   int nk = 0, nq = 0, nb = 0, nocc = 0, ni = 0;
   double omega = 1.0;
   std::vector<int> kmq;

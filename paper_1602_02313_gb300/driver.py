@@ -1,0 +1,117 @@
+"""One GW iteration through the libgw C ABI (host orchestration only; every
+step runs in libgw's kernels).
+
+Order of the steps follows the paper's cycle (Sec. III.B): G(tau) -> for every
+q: P(tau) [Eq. irpol] -> P(i nu) -> W~(i nu) [Eq. tildeW, solved in i nu] ->
+W~(tau) -> Sigma^c(tau) += [Eq. sigc], Sigma^x += [Eq. sigx]; then
+Sigma^c(i w) [Eq. trans] on the sparse set (Dyson) and on the dense set
+(continuation), the diagonal Dyson update of G [Eqs. dysongf-zcjk] and the
+analytic continuation with quasiparticle energies (Sec. III.B.6).
+Screening runs for a batch of q at once (one thread block per (q, nu) system).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (GW_BOSE, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
+               GW_TAU_TO_IW_CONT, GwError)
+
+
+def contraction_flops(nk, nb, ni, ntau):
+    """Algorithmic real flops of one q (8 per complex multiply-add; the Hermitian half of P):
+    P: 4 NI^2 Nb^2 per (k, tau); Sigma^c: 8 NI^2 Nb^2 + 8 NI Nb^2 per (k, tau)."""
+    p = 4.0 * ni * ni * nb * nb * nk * ntau
+    s = (8.0 * ni * ni * nb * nb + 8.0 * ni * nb * nb) * nk * ntau
+    return p, s
+
+
+class Chain:
+    """Buffers and call sequence of one GW iteration on a libgw context."""
+
+    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE):
+        self.ctx = ctx
+        g, cr = ctx.grid, ctx.cr
+        self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
+        self.nnu, self.nw, self.ncont = len(g.nu_idx), len(g.w_idx), g.ncont
+        self.prec = prec
+        self.iqs = list(range(cr.nq)) if iqs is None else list(iqs)
+        self.qb = max(1, min(qb, len(self.iqs)))
+        self.cont_method = cont_method
+        d = dict(device="cuda")
+        f8, c16 = torch.float64, torch.complex128
+        self.eps = eps
+        nk, nb, ni, nt = self.nk, self.nb, self.ni, self.ntau
+        self.G = torch.zeros(nk, nb, nt, dtype=f8, **d)
+        self.occ = torch.zeros(nk, nb, dtype=f8, **d)
+        self.S = torch.zeros(nk, nb, nt, dtype=f8, **d)
+        self.Sx = torch.zeros(nk, nb, dtype=f8, **d)
+        self.P = torch.zeros(self.qb, nt, ni, ni, dtype=c16, **d)
+        self.Piv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
+        self.Wiv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
+        self.Wt = torch.zeros(nt, ni, ni, dtype=c16, **d)
+        self.info = torch.zeros(self.qb, self.nnu, dtype=torch.int32, **d)
+        self.Siw = torch.zeros(nk, nb, self.nw, dtype=c16, **d)
+        self.Siwc = torch.zeros(nk, nb, self.ncont, dtype=c16, **d)
+        self.G1 = torch.zeros_like(self.G)
+        self.occ1 = torch.zeros_like(self.occ)
+        self.eqp = torch.zeros(nk * nb, dtype=f8, **d)
+        self.qinfo = torch.zeros(nk * nb, dtype=torch.int32, **d)
+        self.vxc = None
+        self.timers = None
+
+    def _timed(self, key, fn):
+        if self.timers is None:
+            fn()
+            return
+        s = self.ctx.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        fn()
+        e1.record(s)
+        self.timers.setdefault(key, []).append((e0, e1))
+
+    def start_g0(self):
+        """Reference G0 from the band energies (Sec. III.B.1)."""
+        self.ctx.green_tau(self.eps, self.G, self.occ)
+
+    def sigma(self, G=None, occ=None):
+        """Sigma^c(tau), Sigma^x of the context's q points (accumulated from zero)."""
+        ctx = self.ctx
+        G = self.G if G is None else G
+        occ = self.occ if occ is None else occ
+        self.S.zero_()
+        self.Sx.zero_()
+        ni = self.ni
+        for b0 in range(0, len(self.iqs), self.qb):
+            batch = self.iqs[b0:b0 + self.qb]
+            for j, iq in enumerate(batch):
+                self._timed("polarization", lambda: ctx.polarization(iq, G, self.P[j], self.prec))
+                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j])
+            ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)])
+            for j, iq in enumerate(batch):
+                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt)
+                self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))
+
+    def finish(self, vxc=None):
+        """Sigma(i w), Dyson update, continuation and QP energies from the summed Sigma."""
+        ctx = self.ctx
+        nkb = self.nk * self.nb
+        if vxc is None:
+            vxc = self.Sx  # reference xc potential = Sigma^x[G0] (G0W0 keeps eps~ = eps)
+        ctx.tau_to_freq(GW_FERMI, GW_TAU_TO_IW, nkb, self.S, self.Siw)
+        ctx.tau_to_freq(GW_FERMI, GW_TAU_TO_IW_CONT, nkb, self.S, self.Siwc)
+        ctx.green_tau(self.eps, self.G1, self.occ1, self.Sx, vxc, self.Siw)
+        ctx.continue_(self.cont_method, self.Siwc, self.eps.reshape(-1), self.Sx.reshape(-1),
+                      vxc.reshape(-1), None, None, self.eqp, self.qinfo)
+
+    def step(self):
+        """One G0W0 pass: every row of the hot path over all q of the context."""
+        self.start_g0()
+        self.sigma()
+        self.finish()
+
+    def check(self):
+        ctx = self.ctx
+        ctx.sync()
+        if int(self.info.abs().sum()):
+            raise GwError("zero pivot in a dielectric solve")

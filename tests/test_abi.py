@@ -24,7 +24,7 @@ def gw():
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "gw.h")).read()
-    return sorted(set(re.findall(r"^(?:gw_status|const char\*)\s+(gw_\w+)\(", src, re.M)))
+    return sorted(set(re.findall(r"^(?:gw_status|const char\*|int64_t)\s+(gw_\w+)\(", src, re.M)))
 
 
 def test_exports_every_declared_symbol(gw):
@@ -64,7 +64,7 @@ def test_invalid_arguments_rejected_on_host(gw):
     kmq = np.zeros((1, 8), np.int32)
     v = np.ones((1, 40))
     s = gw._System(1, 8, 1, 16, 8, 40, 1.0, kmq.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
-                   v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None)   # ni = 40 not a multiple of 32
+                   v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 0)   # ni = 40 not a multiple of 32
     h = ctypes.c_void_p()
     assert lib.gw_create(ctypes.byref(h), ctypes.byref(gs), ctypes.byref(s), 0, None) == gw.GW_EINVAL
     assert lib.gw_create(None, ctypes.byref(gs), ctypes.byref(s), 0, None) == gw.GW_EINVAL

@@ -1,0 +1,118 @@
+"""Tensor-core (tcgen05, fp16 hi/lo split, FP32 TMEM accumulation) contractions
+against the FP64 oracle and the FP64 GPU path, called through the C ABI.
+
+Error bars of the split-precision path: each operand carries 22 significant
+bits (two fp16 slices); the accumulation runs in FP32 in tensor memory over
+K segments and is summed in FP64 across segments. The expected max-norm
+relative error is therefore ~sqrt(n_acc) * 2^-24 with n_acc the number of
+FP32 accumulation steps per output (a few 1e-6 at the bench sizes); the
+tolerances below are set from that bound.
+"""
+import numpy as np
+import pytest
+
+import gwinputs as gi
+import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+TOL_P = 2e-5
+TOL_S = 2e-5
+
+
+@pytest.fixture(scope="module")
+def gw():
+    from paper_1602_02313_gb300 import build as b
+    b.build()
+    import paper_1602_02313_gb300 as pkg
+    return pkg
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def zeros(shape, dtype="f8"):
+    import torch
+    return torch.zeros(shape, dtype={"f8": torch.float64, "c16": torch.complex128, "i4": torch.int32}[dtype],
+                       device="cuda")
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def cases():
+    yield "c1", gi.make_config("c1")
+    yield "ragged", (gi.make_crystal(77, 3, 5, 2, 32, 30.0, qlist=[1, 2]), gi.make_grid(30.0, 8, 8, 8, ncont=24))
+    yield "ni160", (gi.make_crystal(78, 8, 12, 5, 160, 50.0, qlist=[3]), gi.make_grid(50.0, 12, 12, 12, ncont=24))
+
+
+@pytest.mark.parametrize("name,case", list(cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_polarization_tc(gw, name, case):
+    cr, gr = case
+    ctx = gw.GW(gr, cr, omega=1.0)
+    G, _ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    for iq in range(cr.nq):
+        P = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+        ctx.polarization(iq, dev(G), P, gw.GW_FP16X2)
+        ctx.sync()
+        ref = orc.polarization(gi.m_for_q(cr, iq), G, cr.kmq[iq])
+        e = rel(host(P), ref)
+        print(f"{name} q{iq}: P tensor-core rel err {e:.3e}")
+        assert e < TOL_P
+        Ph = host(P)
+        assert np.abs(Ph - np.conj(np.swapaxes(Ph, 1, 2))).max() == 0.0
+
+
+@pytest.mark.parametrize("name,case", list(cases()), ids=lambda x: x if isinstance(x, str) else "")
+def test_selfenergy_tc(gw, name, case):
+    cr, gr = case
+    ctx = gw.GW(gr, cr, omega=1.0)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    rng = np.random.default_rng(11)
+    S = zeros((cr.nk, cr.nb, gr.ntau))
+    Sref = np.zeros((cr.nk, cr.nb, gr.ntau))
+    for iq in range(cr.nq):
+        X = rng.standard_normal((gr.ntau, cr.ni, cr.ni)) + 1j * rng.standard_normal((gr.ntau, cr.ni, cr.ni))
+        W = -30.0 * (X @ np.conj(np.swapaxes(X, 1, 2))) / cr.ni
+        ctx.selfenergy(iq, dev(G), dev(occ), dev(W), S, None, gw.GW_FP16X2)
+        sc, _, _ = orc.selfenergy(gi.m_for_q(cr, iq), G, W, cr.v[iq], cr.kmq[iq], occ)
+        Sref += sc
+    ctx.sync()
+    e = rel(host(S), Sref)
+    print(f"{name}: Sigma tensor-core rel err {e:.3e}")
+    assert e < TOL_S
+
+
+def test_c2_full_size_tc_vs_fp64(gw):
+    """Bench sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): tensor-core P and Sigma of
+    one q against the FP64 GPU path (itself pinned to the oracle in test_gpu_parity)."""
+    cr, gr = gi.make_config("c2", qlist=[7])
+    ctx = gw.GW(gr, cr)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    Gd = dev(G)
+    P64 = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    P16 = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    ctx.polarization(0, Gd, P64, gw.GW_FP64)
+    ctx.polarization(0, Gd, P16, gw.GW_FP16X2)
+    ctx.sync()
+    e = rel(host(P16), host(P64))
+    print(f"c2: P tensor-core vs FP64 rel err {e:.3e}")
+    assert e < TOL_P
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((gr.ntau, cr.ni, 16)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 16))
+    W = dev(-(X @ np.conj(np.swapaxes(X, 1, 2))) * 5.0)
+    S64 = zeros((cr.nk, cr.nb, gr.ntau))
+    S16 = zeros((cr.nk, cr.nb, gr.ntau))
+    ctx.selfenergy(0, Gd, dev(occ), W, S64, None, gw.GW_FP64)
+    ctx.selfenergy(0, Gd, dev(occ), W, S16, None, gw.GW_FP16X2)
+    ctx.sync()
+    e = rel(host(S16), host(S64))
+    print(f"c2: Sigma tensor-core vs FP64 rel err {e:.3e}")
+    assert e < TOL_S
