@@ -184,7 +184,8 @@ def main():
     ap.add_argument("--prec", default="fp16x2", choices=["fp16x2", "fp64"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--omega", type=float, default=1.0)
-    ap.add_argument("--nq", type=int, default=0, help="limit q points (exploration only; not a bench line)")
+    ap.add_argument("--nq", type=int, default=0, help="limit q points (profiling / exploration only; not a bench line)")
+    ap.add_argument("--nk", type=int, default=0, help="override Nk (profiling small cases only; not a bench line)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -210,7 +211,7 @@ def main():
     if world > 1:
         dist.barrier()
     prec = gw.PREC[args.prec]
-    full, gr = gi.make_config(args.config)
+    full, gr = gi.make_config(args.config, **({"nk": args.nk} if args.nk > 0 else {}))
     nq = full.nq if args.nq <= 0 else min(args.nq, full.nq)
     per = (nq + world - 1) // world
     q0 = min(rank * per, nq)
@@ -327,7 +328,7 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
                "vs_baseline": None, "dtype": {"fp16x2": "fp16x2 split (fp32 accum) + f64",
                                               "fp64": "f64"}[args.prec],
-               "data": "synthetic", "config": _config(args.config, args, args.prec) | {"nq": nq},
+               "data": "synthetic", "config": _config(args.config, args, args.prec) | {"nq": nq, "nk": cr.nk},
                "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "e2e": e2e,
                "cpu_baseline": cpu}
         print(json.dumps(out))
