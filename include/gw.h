@@ -141,6 +141,24 @@ gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, c
  * (and grows) on first use. */
 gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, double* Wt_iv, int* info);
 
+/* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at the time of the call, such as
+ * code whose device memory was handed to another allocator at start-up, or a loop that must
+ * not take the device-wide synchronisation a cudaMalloc can cause. It needs no context and
+ * allocates nothing (no cudaMalloc / cudaFree, no allocating library call): its scratch is a
+ * 128 MiB array compiled into libgw, which every GPU that loads the library keeps until the
+ * process exits. The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (different streams, or concurrent host threads) race; the solve
+ * overwrites every scratch element it reads, so nothing needs clearing between calls.
+ * Computes exactly what gw_screen does, for nq q points at once:
+ * sqrt_v (device) [nq][ni] = v_I(q)^(1/2); P_iv, Wt_iv cplx [nq][nnu][ni][ni]; info [nq][nnu].
+ * Returns GW_EINVAL if one q point's systems (nnu * ni * 2 ni * 16 bytes) exceed 128 MiB,
+ * GW_ECUDA on a launch error; runs on the cudaStream_t `stream` (NULL = legacy stream). */
+gw_status gw_screen_static(int nq, int nnu, int ni, const double* sqrt_v, const double* P_iv, double* Wt_iv,
+                           int* info, void* stream);
+
 /* Contribution of the iq-th q to the self-energy, ACCUMULATED into the outputs:
  * Eq. (sigc): Sigc_n(k|tau) += -1/(Omega N_k) sum_j G_j(k-q|tau) a_jn^dagger W~(q|tau) a_jn,
  *             a_jn = M[q][k][:][j][n];

@@ -32,7 +32,8 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 # Every symbol declared in include/gw.h.
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
-           "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count"]
+           "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
+           "gw_screen_static"]
 
 
 class GwError(RuntimeError):
@@ -106,6 +107,7 @@ def load_library(path=LIB_PATH):
         "gw_copy_m": [vp, i32, i32, i32, vp],
         "gw_transform_matrices": [ctypes.POINTER(_Grid), vp, vp, vp, vp, vp],
         "gw_launch_count": [vp],
+        "gw_screen_static": [i32, i32, i32, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

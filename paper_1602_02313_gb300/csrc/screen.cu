@@ -8,6 +8,9 @@
 // submatrix is nonsingular. A zero pivot is still detected and reported in info.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <string>
+
 #include "gw_internal.h"
 
 namespace gwi {
@@ -112,3 +115,47 @@ gw_status launch_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W,
 }
 
 }  // namespace gwi
+
+// ---------------------------------------------------------------------------
+// gw_screen_static: the same solve with its scratch in a file-scope device
+// array, for callers that must not allocate device memory. The array is part
+// of the library image: every GPU that loads libgw holds it until the process
+// exits. Its device address is looked up once per device (cudaGetSymbolAddress
+// with that device current) on the first call there.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kScreenStaticBytes = 128ull << 20;  // 128 MiB
+static __device__ __align__(256) unsigned char g_screen_scratch[kScreenStaticBytes];
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" gw_status gw_screen_static(int nq, int nnu, int ni, const double* sqrt_v, const double* P_iv,
+                                      double* Wt_iv, int* info, void* stream) {
+  if (nq < 1 || nnu < 1 || ni < 1 || !sqrt_v || !P_iv || !Wt_iv || !info) return GW_EINVAL;
+  const size_t per_q = (size_t)nnu * ni * 2 * ni * sizeof(double2);
+  if (per_q > kScreenStaticBytes) return GW_EINVAL;  // one q point's systems must fit the scratch
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GW_ECUDA;
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_screen_scratch) != cudaSuccess || !p) return GW_ECUDA;
+      g_scratch_ptr[dev] = p;
+    }
+    scratch = g_scratch_ptr[dev];
+  }
+  const int qpp = (int)(kScreenStaticBytes / per_q);  // q points per pass
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int q0 = 0; q0 < nq; q0 += qpp) {
+    const int cq = nq - q0 < qpp ? nq - q0 : qpp;
+    const size_t sys0 = (size_t)q0 * nnu;
+    gwi::k_screen<<<cq * nnu, 512, 0, st>>>((const double2*)P_iv + sys0 * ni * ni, sqrt_v + (size_t)q0 * ni, nnu, ni,
+                                      (double2*)scratch, (double2*)Wt_iv + sys0 * ni * ni, info + sys0);
+    if (cudaGetLastError() != cudaSuccess) return GW_ECUDA;
+  }
+  return GW_OK;
+}
