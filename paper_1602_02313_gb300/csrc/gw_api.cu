@@ -294,34 +294,58 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int64_t batch, const do
 
 // ----------------------------------------------------------------------------
 // Exchange self-energy, product-basis form of Eq. (sigx) with diagonal v:
-// Sigx_n(k) += -1/(Omega Nk) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2. One block per k,
-// threads over n; deterministic (no atomics).
+// Sigx_n(k) += -1/(Omega Nk) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2.
+// k_vm streams M once, coalesced along the pair index p = j nb + n:
+// vm[k][p] = sum_I v_I |M^I_p|^2; k_sigx_occ then contracts with the occupations.
+// Deterministic (no atomics).
 // ----------------------------------------------------------------------------
-__global__ void k_sigx(const double2* __restrict__ M, const double* __restrict__ v, const int* __restrict__ kmq,
-                       const double* __restrict__ occ, int nk, int ni, int nb, double pref, double* __restrict__ Sx) {
-  const int k = blockIdx.x;
-  const double2* Mk = M + (size_t)k * ni * nb * nb;
-  const int km = kmq[k];
-  for (int n = threadIdx.x; n < nb; n += blockDim.x) {
-    double s = 0.0;
-    for (int j = 0; j < nb; ++j) {
-      const double f = occ[(size_t)km * nb + j];
-      double t = 0.0;
-      for (int I = 0; I < ni; ++I) {
-        const double2 m = Mk[((size_t)I * nb + j) * nb + n];
-        t = fma(v[I], m.x * m.x + m.y * m.y, t);
-      }
-      s = fma(f, t, s);
-    }
-    Sx[(size_t)k * nb + n] += pref * s;
+__global__ void k_vm(const double2* __restrict__ M, const double* __restrict__ v, int ni, int np,
+                     double* __restrict__ vm) {
+  const int k = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const double2* Mk = M + (size_t)k * ni * np + p;
+  double s = 0.0;
+  for (int I = 0; I < ni; ++I) {
+    const double2 m = Mk[(size_t)I * np];
+    s = fma(v[I], fma(m.x, m.x, m.y * m.y), s);
   }
+  vm[(size_t)k * np + p] = s;
+}
+
+__global__ void k_sigx_occ(const double* __restrict__ vm, const int* __restrict__ kmq, const double* __restrict__ occ,
+                           int nk, int nb, double pref, double* __restrict__ Sx) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nk * nb) return;
+  const int k = e / nb, n = e % nb;
+  const double* vk = vm + (size_t)k * nb * nb;
+  const double* f = occ + (size_t)kmq[k] * nb;
+  double s = 0.0;
+  for (int j = 0; j < nb; ++j) s = fma(f[j], vk[j * nb + n], s);
+  Sx[e] += pref * s;
 }
 
 gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx) {
-  const double2* M = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * c->nb * c->nb;
-  k_sigx<<<c->nk, 128, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->d_kmq + (size_t)iq * c->nk, occ, c->nk,
-                                       c->ni, c->nb, -1.0 / (c->omega * c->nk), Sx);
-  return check_launch(c, "sigx");
+  const int np = c->nb * c->nb;
+  const size_t need = (size_t)c->nk * np * sizeof(double);
+  if (need > c->vm_bytes) {
+    if (c->d_vm) cudaFree(c->d_vm);
+    c->d_vm = nullptr;
+    c->vm_bytes = 0;
+    if (cudaMalloc((void**)&c->d_vm, need) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, GW_ENOMEM, "sigx workspace");
+    }
+    c->vm_bytes = need;
+  }
+  const double2* M = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
+  k_vm<<<dim3((np + 255) / 256, c->nk), 256, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->ni, np, c->d_vm);
+  gw_status s = check_launch(c, "sigx_vm");
+  if (s != GW_OK) return s;
+  const int n = c->nk * c->nb;
+  k_sigx_occ<<<(n + 127) / 128, 128, 0, c->stream>>>(c->d_vm, c->d_kmq + (size_t)iq * c->nk, occ, c->nk, c->nb,
+                                                     -1.0 / (c->omega * c->nk), Sx);
+  return check_launch(c, "sigx_occ");
 }
 
 }  // namespace gwi
@@ -455,7 +479,7 @@ gw_status gw_destroy(gw_ctx* c) {
   cudaDeviceSynchronize();
   double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
                     c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_b,
-                    c->d_pade};
+                    c->d_pade,  c->d_vm};
   for (double* p : bufs)
     if (p) cudaFree(p);
   if (c->d_kmq) cudaFree(c->d_kmq);

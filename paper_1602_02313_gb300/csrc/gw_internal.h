@@ -73,6 +73,9 @@ struct gw_ctx {
   double* d_Bbwd = nullptr;    // [ntau][2 nnu]
   double* d_Fbwd = nullptr;    // [ntau][2 nw]
   double* d_Fbwd_beta = nullptr;
+  // exchange workspace: vm[k][p] = sum_I v_I |M^I_p|^2
+  double* d_vm = nullptr;
+  size_t vm_bytes = 0;
   // screening workspace: augmented systems [nsys][ni][2 ni] cplx
   double* d_aug = nullptr;
   size_t aug_bytes = 0;

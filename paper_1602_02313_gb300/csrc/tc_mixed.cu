@@ -65,15 +65,27 @@ struct alignas(16) h8 {
 };
 
 // --------------------------------------------------------------------------- polarization
+// The upper triangle of P is covered by "strips": rows [128 i, 128 i + 128) x columns
+// [c0, c0 + N), c0 >= 128 i, N <= 256. A work unit is (K segment, strip, tau). The unscaled
+// operand Y (rows of the strip's columns) is bulk-copied from YS, a pre-split,
+// pre-swizzled image of M[q]:
+//   YS[k][chunk][iblk][slice][128 rows x 128 B], row = [Re A (32 pairs) | Im A (32 pairs)],
+// slices hi, lo. The scaled operand X = w_tau(p) A (rows of the strip) is built by the
+// producer warps from the same image. TMEM holds Re P (N columns) and Im P (N columns).
 constexpr int kPolChunksPerSeg = 32;
-constexpr int PT_THREADS = 288;  // warps 0-7 produce, warp 8 issues MMAs; warps 0-3 run the epilogue
-constexpr int P_STAGE_BYTES = 6 * 16384;  // Yh Yl Xh0 Xl0 Xh1 Xl1, 128 rows x 128 B each
+constexpr int PT_THREADS = 288;                     // warps 0-7 produce / run the epilogue, warp 8 issues MMAs
+constexpr int P_XT = 16384;                         // one X slice: 128 rows x 128 B
+constexpr int P_STAGE_BYTES = 2 * P_XT + 2 * 256 * 128;  // X hi, lo (128 rows) + Y hi, lo (<= 256 rows)
 
 struct PolSmem {
   uint64_t full[2], empty[2], done;
   uint32_t tslot;
   int abort_flag;
 };
+
+__device__ __forceinline__ size_t ys_tile(int k, int c, int iblk, int sl, int cpk, int nib) {
+  return ((((size_t)k * cpk + c) * nib + iblk) * 2 + sl) * (size_t)(128 * 64);  // in halves
+}
 
 // Pair weights of Eq. (irpol): wt[k][tau][p] = Q_ab(tau) = -G_b(k|tau) G_a(k-q|beta - tau),
 // p = a nb + b, rows padded to npw (multiple of 32) with zeros.
@@ -90,26 +102,56 @@ __global__ void k_pol_weights(const double* __restrict__ G, const int* __restric
   wt[e] = w;
 }
 
+// M[q] -> YS (scaled by kScaleA, split into fp16 hi / lo). One thread per (k, I, 8 pairs).
+__global__ void k_split_y(const double2* __restrict__ Mq, int nk, int ni, int np, int cpk, int nib,
+                          __half* __restrict__ YS) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = (int64_t)nk * ni * cpk * 4;
+  if (e >= n) return;
+  const int g8 = (int)(e & 3);
+  const int c = (int)((e >> 2) % cpk);
+  const int I = (int)((e / (4 * cpk)) % ni);
+  const int k = (int)(e / ((int64_t)4 * cpk * ni));
+  const int pb = c * 32 + 8 * g8;
+  h8 rh, rl, ih, il;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    double2 v = make_double2(0.0, 0.0);
+    if (pb + q < np) v = Mq[((size_t)k * ni + I) * np + pb + q];
+    split2((float)v.x * kScaleA, rh.v[q], rl.v[q]);
+    split2((float)v.y * kScaleA, ih.v[q], il.v[q]);
+  }
+  const int iblk = I >> 7, r = I & 127;
+  __half* hi = YS + ys_tile(k, c, iblk, 0, cpk, nib);
+  __half* lo = YS + ys_tile(k, c, iblk, 1, cpk, nib);
+  *reinterpret_cast<h8*>(hi + sw128_off(r, 8 * g8) / 2) = rh;
+  *reinterpret_cast<h8*>(hi + sw128_off(r, 32 + 8 * g8) / 2) = ih;
+  *reinterpret_cast<h8*>(lo + sw128_off(r, 8 * g8) / 2) = rl;
+  *reinterpret_cast<h8*>(lo + sw128_off(r, 32 + 8 * g8) / 2) = il;
+}
+
 __global__ void __launch_bounds__(PT_THREADS, 1)
-    k_pol_tc(const double2* __restrict__ Mq, const float* __restrict__ wt, int nk, int ni, int nb, int ntau,
-             int npw, int ntiles, const int2* __restrict__ tiles, int nseg, float* __restrict__ part,
+    k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
+             int npw, int nstrips, const int4* __restrict__ strips, int nseg, float* __restrict__ part,
              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntp = ntau / 2;
   const int u = blockIdx.x;
-  const int tp = u % ntp, tile = (u / ntp) % ntiles, seg = u / (ntp * ntiles);
-  const int ti = tiles[tile].x, tj = tiles[tile].y;
-  const int np = nb * nb, cpk = (np + 31) / 32, total = nk * cpk;
+  const int it = u % ntau, strip = (u / ntau) % nstrips, seg = u / (ntau * nstrips);
+  const int4 sd = strips[strip];                 // (row block, c0, N, -)
+  const int xb = sd.x, c0 = sd.y, N = sd.z;
+  const int nib = (ni + 127) / 128;
+  const int total = nk * cpk;
   const int L = (total + nseg - 1) / nseg;
   const int g0 = seg * L, g1 = min(total, g0 + L);
   const int nchunk = max(0, g1 - g0);
+  const uint32_t ybytes_slice = (uint32_t)N * 128;
 
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.full[s], 256);
+      mbar_init(&S.full[s], 257);
       mbar_init(&S.empty[s], 1);
     }
     mbar_init(&S.done, 1);
@@ -128,67 +170,42 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       const int s = i & 1;
       if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
       unsigned char* st = base + s * P_STAGE_BYTES;
-      const int g = g0 + i, k = g / cpk, p0 = (g % cpk) * 32;
-      const double2* Mk = Mq + (size_t)k * ni * np;
+      const int g = g0 + i, k = g / cpk, c = g % cpk;
+      if (tid == 0) {
+        // Y: rows [c0, c0 + N) = whole or leading parts of 128-row blocks, hi and lo slices
+        mbar_arrive_expect_tx(&S.full[s], 2 * ybytes_slice);
+        for (int r0 = 0; r0 < N; r0 += 128) {
+          const int rows = min(128, N - r0);
+          const int yb = (c0 + r0) >> 7;
+          for (int sl = 0; sl < 2; ++sl)
+            bulk_g2s(st + 2 * P_XT + sl * ybytes_slice + r0 * 128, YS + ys_tile(k, c, yb, sl, cpk, nib),
+                     (uint32_t)rows * 128, &S.full[s]);
+        }
+      }
+      // X = w A for the strip's 128 rows: 512 items of (row, 8 pairs)
+      const __half* xh = YS + ys_tile(k, c, xb, 0, cpk, nib);
+      const __half* xl = YS + ys_tile(k, c, xb, 1, cpk, nib);
+      const float* wrow = wt + ((size_t)k * ntau + it) * npw + c * 32;
       for (int item = tid; item < 512; item += 256) {
         const int r = item >> 2, gq = item & 3;
-        const int pb = p0 + 8 * gq;
-        // Y rows (block tj)
-        float yr[8], yi[8];
-        {
-          const int I = tj * 128 + r;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            double2 v = make_double2(0.0, 0.0);
-            if (I < ni && pb + e < np) v = __ldg(&Mk[(size_t)I * np + pb + e]);
-            yr[e] = (float)v.x * kScaleA;
-            yi[e] = (float)v.y * kScaleA;
-          }
-        }
-        float xr[8], xi[8];
-        if (ti == tj) {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            xr[e] = yr[e];
-            xi[e] = yi[e];
-          }
-        } else {
-          const int I = ti * 128 + r;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            double2 v = make_double2(0.0, 0.0);
-            if (I < ni && pb + e < np) v = __ldg(&Mk[(size_t)I * np + pb + e]);
-            xr[e] = (float)v.x * kScaleA;
-            xi[e] = (float)v.y * kScaleA;
-          }
-        }
         const uint32_t oRe = sw128_off(r, 8 * gq), oIm = sw128_off(r, 32 + 8 * gq);
-        h8 hr, lr, hi_, li;
+        const h8 rh = *reinterpret_cast<const h8*>(xh + oRe / 2);
+        const h8 rl = *reinterpret_cast<const h8*>(xl + oRe / 2);
+        const h8 ih = *reinterpret_cast<const h8*>(xh + oIm / 2);
+        const h8 il = *reinterpret_cast<const h8*>(xl + oIm / 2);
+        const float4 w0 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * gq));
+        const float4 w1 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * gq) + 1);
+        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        h8 orh, orl, oih, oil;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          split2(yr[e], hr.v[e], lr.v[e]);
-          split2(yi[e], hi_.v[e], li.v[e]);
+          split2(wv[e] * (__half2float(rh.v[e]) + __half2float(rl.v[e])), orh.v[e], orl.v[e]);
+          split2(wv[e] * (__half2float(ih.v[e]) + __half2float(il.v[e])), oih.v[e], oil.v[e]);
         }
-        *reinterpret_cast<h8*>(st + 0 * 16384 + oRe) = hr;
-        *reinterpret_cast<h8*>(st + 0 * 16384 + oIm) = hi_;
-        *reinterpret_cast<h8*>(st + 1 * 16384 + oRe) = lr;
-        *reinterpret_cast<h8*>(st + 1 * 16384 + oIm) = li;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const float4* wp = reinterpret_cast<const float4*>(wt + ((size_t)k * ntau + 2 * tp + j) * npw + pb);
-          const float4 w0 = __ldg(wp), w1 = __ldg(wp + 1);
-          const float wv8[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const float wv = wv8[e];
-            split2(wv * xr[e], hr.v[e], lr.v[e]);
-            split2(wv * xi[e], hi_.v[e], li.v[e]);
-          }
-          *reinterpret_cast<h8*>(st + (2 + 2 * j) * 16384 + oRe) = hr;
-          *reinterpret_cast<h8*>(st + (2 + 2 * j) * 16384 + oIm) = hi_;
-          *reinterpret_cast<h8*>(st + (3 + 2 * j) * 16384 + oRe) = lr;
-          *reinterpret_cast<h8*>(st + (3 + 2 * j) * 16384 + oIm) = li;
-        }
+        *reinterpret_cast<h8*>(st + oRe) = orh;
+        *reinterpret_cast<h8*>(st + oIm) = oih;
+        *reinterpret_cast<h8*>(st + P_XT + oRe) = orl;
+        *reinterpret_cast<h8*>(st + P_XT + oIm) = oil;
       }
       fence_proxy_async_smem();
       mbar_arrive(&S.full[s]);
@@ -196,52 +213,51 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_f16(128, 128, false, false), idn = idesc_f16(128, 128, false, true);
+    const uint32_t id = idesc_f16(128, N, false, false), idn = idesc_f16(128, N, false, true);
+    const uint32_t dre = tbase, dim = tbase + N;
     for (int i = 0; i < nchunk; ++i) {
       const int s = i & 1;
       if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(base + s * P_STAGE_BYTES);
-      const uint32_t yh = st, yl = st + 16384;
+      const uint32_t xh = st, xl = st + P_XT, yh = st + 2 * P_XT, yl = yh + ybytes_slice;
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const uint32_t xh = st + (2 + 2 * j) * 16384, xl = st + (3 + 2 * j) * 16384;
-        const uint32_t dre = tbase + j * 256, dim = tbase + j * 256 + 128;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
-          const uint32_t bo = 32 * ks;
-          mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yh + bo), id, acc);
-          mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yl + bo), id, 1);
-          mma_f16(dre, sdesc_sw128(xl + bo), sdesc_sw128(yh + bo), id, 1);
-          const uint32_t ao = 32 * ((ks + 2) & 3);
-          const uint32_t idx = ks < 2 ? id : idn;
-          mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yh + bo), idx, acc);
-          mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yl + bo), idx, 1);
-          mma_f16(dim, sdesc_sw128(xl + ao), sdesc_sw128(yh + bo), idx, 1);
-        }
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
+        const uint32_t bo = 32 * ks;
+        mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yh + bo), id, acc);
+        mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yl + bo), id, 1);
+        mma_f16(dre, sdesc_sw128(xl + bo), sdesc_sw128(yh + bo), id, 1);
+        // Im P = [w Im A | -w Re A] . [Re A | Im A]: other K half of X, negated for the second half
+        const uint32_t ao = 32 * ((ks + 2) & 3);
+        const uint32_t idx = ks < 2 ? id : idn;
+        mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yh + bo), idx, acc);
+        mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yl + bo), idx, 1);
+        mma_f16(dim, sdesc_sw128(xl + ao), sdesc_sw128(yh + bo), idx, 1);
       }
       mma_commit(&S.empty[s]);
     }
     mma_commit(&S.done);
   }
 
-  // ------------------------------------------------------------ epilogue: FP32 partial tiles
-  if (warp < 4) {
+  // ------------------------------------------------------------ epilogue: FP32 partial strips (8 warps)
+  if (warp < 8) {
     const bool ok = nchunk > 0 && wait_bar(&S.done, 0, &S.abort_flag, err);
     tc_fence_after();
-    const int row = 32 * warp + lane;
-    float* out = part + (size_t)u * 4 * 128 * 128;
-    for (int acc = 0; acc < 4; ++acc) {
-      for (int c = 0; c < 128; c += 16) {
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = 32 * quad + lane;
+    float* out = part + (size_t)u * 2 * 128 * 256;
+    const int nb16 = N / 16;
+    for (int acc = 0; acc < 2; ++acc) {
+      for (int bk = half; bk < nb16; bk += 2) {
         float v[16];
         if (ok) {
-          tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + acc * 128 + c, v);
+          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + acc * N + 16 * bk, v);
         } else {
 #pragma unroll
           for (int e = 0; e < 16; ++e) v[e] = 0.f;
         }
-        float4* o = reinterpret_cast<float4*>(out + ((size_t)acc * 128 + row) * 128 + c);
+        float4* o = reinterpret_cast<float4*>(out + ((size_t)acc * 128 + row) * 256 + 16 * bk);
 #pragma unroll
         for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
       }
@@ -252,39 +268,70 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   if (warp == 8) tmem_dealloc(tbase, 512);
 }
 
-// Sum the FP32 partial tiles over K segments in FP64 and write the Hermitian P.
-__global__ void k_pol_reduce(const float* __restrict__ part, int ni, int ntau, int nt128, const int* __restrict__ tile_of,
-                             int ntiles, int nseg, double scale, double2* __restrict__ P) {
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t tot = (int64_t)ntau * ni * ni;
-  if (e >= tot) return;
-  const int it = (int)(e / ((int64_t)ni * ni));
-  const int I = (int)((e / ni) % ni), J = (int)(e % ni);
-  // upper triangle from the tiles; the lower triangle mirrors it (exactly Hermitian)
-  int a = I, b = J;
-  bool conj = false;
-  if (I > J) {
-    a = J;
-    b = I;
-    conj = true;
+// Sum the FP32 partial strips over K segments in FP64 and write the Hermitian P.
+// One block per (32 x 32 block (ab, bb) with ab <= bb, tau); reads are coalesced along
+// the column, the mirrored lower triangle is written through a shared-memory transpose.
+__global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ part, int ni, int ntau,
+                                                    const int* __restrict__ strip_of, int nstrips,
+                                                    const int4* __restrict__ strips, int nseg, double scale,
+                                                    double2* __restrict__ P) {
+  __shared__ double2 tr[32][33];
+  const int nb32 = (ni + 31) / 32;
+  int t = blockIdx.x, ab = 0;
+  while (t >= nb32 - ab) {
+    t -= nb32 - ab;
+    ++ab;
   }
-  const int tile = tile_of[(a / 128) * nt128 + (b / 128)];
-  const int ntp = ntau / 2, tp = it / 2, j = it & 1;
-  double re = 0.0, im = 0.0;
+  const int bb = ab + t;
+  const int it = blockIdx.y;
+  const int strip = strip_of[ab * nb32 + bb];
+  const int4 sd = strips[strip];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int b = bb * 32 + tx;
+  double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
   for (int s = 0; s < nseg; ++s) {
-    const int u = (s * ntiles + tile) * ntp + tp;
-    const float* p = part + (size_t)u * 4 * 128 * 128;
-    re += (double)p[((size_t)(2 * j) * 128 + (a & 127)) * 128 + (b & 127)];
-    im += (double)p[((size_t)(2 * j + 1) * 128 + (a & 127)) * 128 + (b & 127)];
+    const int u = (s * nstrips + strip) * ntau + it;
+    const float* pre = part + (size_t)u * 2 * 128 * 256;
+    const float* pim = pre + 128 * 256;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int a = ab * 32 + ty + 8 * r;
+      const size_t o = (size_t)(a & 127) * 256 + (b - sd.y);
+      re[r] += (double)pre[o];
+      im[r] += (double)pim[o];
+    }
   }
-  // Im P_II = 0 exactly for a Hermitian P (the tensor-core sum leaves O(2^-22) residue)
-  P[e] = make_double2(re * scale, I == J ? 0.0 : (conj ? -im : im) * scale);
+  double2* Pt = P + (size_t)it * ni * ni;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int a = ab * 32 + ty + 8 * r;
+    double2 v = make_double2(re[r] * scale, im[r] * scale);
+    if (a == b) v.y = 0.0;  // Im P_II = 0 exactly (the tensor-core sum leaves O(2^-22) residue)
+    if (a < ni && b < ni && (ab < bb || a <= b)) Pt[(size_t)a * ni + b] = v;
+    tr[ty + 8 * r][tx] = make_double2(v.x, -v.y);
+  }
+  __syncthreads();
+  // lower triangle: P[b'][a'] = conj(P[a'][b']) for a' < b'
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int row = bb * 32 + ty + 8 * r;  // b'
+    const int col = ab * 32 + tx;          // a'
+    if (row < ni && col < ni && col < row) Pt[(size_t)row * ni + col] = tr[tx][ty + 8 * r];
+  }
 }
 
 // --------------------------------------------------------------------------- self-energy
-// Split M[q] into the pair-major fp16 slices XT[slice][k][p][I] (slices: Re hi, Re lo,
-// Im hi, Im lo; rows p >= nb^2 zero), via a 32 x 32 shared-memory transpose.
-__global__ void k_split_x(const double2* __restrict__ Mq, int nk, int ni, int np, int npp, __half* __restrict__ XT) {
+// Operand slices live in global memory as ready-made shared-memory images: each 32-wide
+// K chunk of a tile is stored in the 64-byte-swizzled K-major layout, so one bulk copy
+// per operand and chunk fills a pipeline stage.
+//   XS[k][pblk][kc][slice][128 rows x 64 B]   slices: Re hi, Re lo, Im hi, Im lo of M (rows = pairs p)
+//   WS[tau][kc][slice][ni rows x 64 B]        slices: Re hi, Re lo, 2 Im hi, 2 Im lo of W~(tau)
+__device__ __forceinline__ size_t xs_tile(int k, int pblk, int kc, int sl, int npb, int nkc) {
+  return ((((size_t)k * npb + pblk) * nkc + kc) * 4 + sl) * (size_t)(128 * 32);  // in halves
+}
+
+// Split M[q] into XS via a 32 x 32 shared-memory transpose (rows p >= nb^2 zero).
+__global__ void k_split_x(const double2* __restrict__ Mq, int ni, int np, int npb, __half* __restrict__ XS) {
   __shared__ double2 tileS[32][33];
   const int k = blockIdx.z;
   const int p0 = blockIdx.x * 32, I0 = blockIdx.y * 32;
@@ -294,160 +341,154 @@ __global__ void k_split_x(const double2* __restrict__ Mq, int nk, int ni, int np
     tileS[r][tx] = (I < ni && p < np) ? Mq[((size_t)k * ni + I) * np + p] : make_double2(0.0, 0.0);
   }
   __syncthreads();
-  const size_t slice = (size_t)nk * npp * ni;
+  const int nkc = ni / 32;
   for (int r = ty; r < 32; r += 8) {
     const int p = p0 + r, I = I0 + tx;
-    if (p >= npp || I >= ni) continue;
     const double2 v = tileS[tx][r];
     __half rh, rl, ih, il;
     split2((float)v.x * kScaleA, rh, rl);
     split2((float)v.y * kScaleA, ih, il);
-    const size_t o = ((size_t)k * npp + p) * ni + I;
-    XT[o] = rh;
-    XT[slice + o] = rl;
-    XT[2 * slice + o] = ih;
-    XT[3 * slice + o] = il;
+    const int pblk = p >> 7, row = p & 127, kc = I >> 5, col = I & 31;
+    const size_t o = sw64_off(row, col) / 2;
+    XS[xs_tile(k, pblk, kc, 0, npb, nkc) + o] = rh;
+    XS[xs_tile(k, pblk, kc, 1, npb, nkc) + o] = rl;
+    XS[xs_tile(k, pblk, kc, 2, npb, nkc) + o] = ih;
+    XS[xs_tile(k, pblk, kc, 3, npb, nkc) + o] = il;
   }
 }
 
-// Split W~(tau) into BW[slice][tau][I][I'] (slices: Re hi, Re lo, 2 Im hi, 2 Im lo).
-__global__ void k_split_w(const double2* __restrict__ W, int ntau, int ni, __half* __restrict__ BW) {
+// Split W~(tau) into WS.
+__global__ void k_split_w(const double2* __restrict__ W, int ntau, int ni, __half* __restrict__ WS) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = (int64_t)ntau * ni * ni;
   if (e >= n) return;
+  const int it = (int)(e / ((int64_t)ni * ni)), I = (int)((e / ni) % ni), J = (int)(e % ni);
   const double2 w = W[e];
   __half a, b, c, d;
   split2((float)w.x * kScaleW, a, b);
   split2((float)(2.0 * w.y) * kScaleW, c, d);
-  BW[e] = a;
-  BW[n + e] = b;
-  BW[2 * n + e] = c;
-  BW[3 * n + e] = d;
+  const int nkc = ni / 32, kc = J >> 5;
+  const size_t tile = (size_t)ni * 32;  // halves per slice tile
+  const size_t base = ((size_t)it * nkc + kc) * 4 * tile + sw64_off(I, J & 31) / 2;
+  WS[base] = a;
+  WS[base + tile] = b;
+  WS[base + 2 * tile] = c;
+  WS[base + 3 * tile] = d;
 }
 
-constexpr int ST_THREADS = 416;  // warps 0-3 epilogue, 4-11 produce, 12 issues MMAs
-constexpr int S_ATILE = 128 * 64;  // 128 rows x 64 B (32 fp16)
+constexpr int ST_EPI_WARPS = 16;                    // 4 per TMEM lane quadrant
+constexpr int ST_THREADS = (ST_EPI_WARPS + 2) * 32;  // + producer warp + MMA warp
+constexpr int S_ATILE = 128 * 64;                   // 128 rows x 64 B (32 fp16)
 
 struct SigSmem {
   uint64_t full[2], empty[2], tfull, tempty;
   uint32_t tslot;
   int abort_flag;
+  float red[4][128];
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 1)
-    k_sig_tc(const __half* __restrict__ XT, const __half* __restrict__ BW, int nk, int ni, int npp, int ntau,
+    k_sig_tc(const __half* __restrict__ XS, const __half* __restrict__ WS, int ni, int npb, int ntau,
              double* __restrict__ D, int np, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  const int BT = ni * 64;                 // one B slice tile: ni rows x 64 B
-  const int stage_bytes = 4 * S_ATILE + 4 * BT;
+  const int BT = ni * 64;  // one W slice tile: ni rows x 64 B
+  const int a_bytes = 4 * S_ATILE, b_bytes = 4 * BT;
+  const int stage_bytes = a_bytes + b_bytes;
   SigSmem& S = *reinterpret_cast<SigSmem*>(base + 2 * stage_bytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pblk = blockIdx.x, k = blockIdx.y;
   const int nkc = ni / 32;
   const int nchunk = ntau * nkc;
-  const size_t xslice = (size_t)nk * npp * ni;
-  const size_t wslice = (size_t)ntau * ni * ni;
+  const int PW = ST_EPI_WARPS, MW = ST_EPI_WARPS + 1;
 
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.full[s], 256);
+      mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
     mbar_init(&S.tfull, 1);
-    mbar_init(&S.tempty, 128);
+    mbar_init(&S.tempty, ST_EPI_WARPS * 32);
     S.abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 12) tmem_alloc(&S.tslot, 512);
+  if (warp == MW) tmem_alloc(&S.tslot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = S.tslot;
 
-  if (warp >= 4 && warp < 12) {
-    // ------------------------------------------------------------ producers
-    const int pt = tid - 128;
-    for (int i = 0; i < nchunk; ++i) {
-      const int s = i & 1;
-      if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
-      unsigned char* st = base + s * stage_bytes;
-      const int it = i / nkc, kc = i % nkc;
-      // A tiles: 4 slices x 128 rows x 4 chunks of 16 B
-      for (int e = pt; e < 4 * 128 * 4; e += 256) {
-        const int sl = e >> 9, r = (e >> 2) & 127, c = e & 3;
-        const int p = pblk * 128 + r;
-        const __half* src = XT + sl * xslice + ((size_t)k * npp + p) * ni + kc * 32 + 8 * c;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
-        *reinterpret_cast<uint4*>(st + sl * S_ATILE + sw64_off(r, 8 * c)) = v;
+  if (warp == PW) {
+    // ------------------------------------------------------------ producer: two bulk copies per chunk
+    if (lane == 0) {
+      for (int i = 0; i < nchunk; ++i) {
+        const int s = i & 1;
+        if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
+        const int it = i / nkc, kc = i % nkc;
+        unsigned char* st = base + s * stage_bytes;
+        mbar_arrive_expect_tx(&S.full[s], (uint32_t)stage_bytes);
+        bulk_g2s(st, XS + xs_tile(k, pblk, kc, 0, npb, nkc), (uint32_t)a_bytes, &S.full[s]);
+        bulk_g2s(st + a_bytes, WS + ((size_t)it * nkc + kc) * 4 * ((size_t)ni * 32), (uint32_t)b_bytes, &S.full[s]);
       }
-      // B tiles: 4 slices x ni rows x 4 chunks
-      for (int e = pt; e < 4 * ni * 4; e += 256) {
-        const int sl = e / (ni * 4), rem = e % (ni * 4), r = rem >> 2, c = rem & 3;
-        const __half* src = BW + sl * wslice + ((size_t)it * ni + r) * ni + kc * 32 + 8 * c;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(src));
-        *reinterpret_cast<uint4*>(st + 4 * S_ATILE + sl * BT + sw64_off(r, 8 * c)) = v;
-      }
-      fence_proxy_async_smem();
-      mbar_arrive(&S.full[s]);
-      if (S.abort_flag) break;
     }
-  } else if (warp == 12 && lane == 0) {
+  } else if (warp == MW) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_f16(128, ni, false, false);
-    const uint32_t y1 = tbase, y2 = tbase + ni;
-    for (int i = 0; i < nchunk; ++i) {
-      const int s = i & 1, it = i / nkc, kc = i % nkc;
-      if (kc == 0 && it > 0 && !wait_bar(&S.tempty, (it - 1) & 1, &S.abort_flag, err)) break;
-      if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) break;
-      tc_fence_after();
-      const uint32_t st = smem_u32(base + s * stage_bytes);
-      const uint32_t arh = st, arl = st + S_ATILE, aih = st + 2 * S_ATILE, ail = st + 3 * S_ATILE;
-      const uint32_t bb = st + 4 * S_ATILE;
-      const uint32_t wrh = bb, wrl = bb + BT, wih = bb + 2 * BT, wil = bb + 3 * BT;
+    if (lane == 0) {
+      const uint32_t id = idesc_f16(128, ni, false, false);
+      const uint32_t y1 = tbase, y2 = tbase + ni;
+      for (int i = 0; i < nchunk; ++i) {
+        const int s = i & 1, it = i / nkc, kc = i % nkc;
+        if (kc == 0 && it > 0 && !wait_bar(&S.tempty, (it - 1) & 1, &S.abort_flag, err)) break;
+        if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) break;
+        tc_fence_after();
+        const uint32_t st = smem_u32(base + s * stage_bytes);
+        const uint32_t arh = st, arl = st + S_ATILE, aih = st + 2 * S_ATILE, ail = st + 3 * S_ATILE;
+        const uint32_t bb = st + a_bytes;
+        const uint32_t wrh = bb, wrl = bb + BT, wih = bb + 2 * BT, wil = bb + 3 * BT;
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) {
-        const uint32_t o = 32 * ks;
-        const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
-        mma_f16(y1, sdesc_sw64(arh + o), sdesc_sw64(wrh + o), id, acc);
-        mma_f16(y1, sdesc_sw64(arh + o), sdesc_sw64(wrl + o), id, 1);
-        mma_f16(y1, sdesc_sw64(arl + o), sdesc_sw64(wrh + o), id, 1);
-        mma_f16(y2, sdesc_sw64(aih + o), sdesc_sw64(wrh + o), id, acc);
-        mma_f16(y2, sdesc_sw64(aih + o), sdesc_sw64(wrl + o), id, 1);
-        mma_f16(y2, sdesc_sw64(ail + o), sdesc_sw64(wrh + o), id, 1);
-        mma_f16(y2, sdesc_sw64(arh + o), sdesc_sw64(wih + o), id, 1);
-        mma_f16(y2, sdesc_sw64(arh + o), sdesc_sw64(wil + o), id, 1);
-        mma_f16(y2, sdesc_sw64(arl + o), sdesc_sw64(wih + o), id, 1);
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint32_t o = 32 * ks;
+          const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+          mma_f16(y1, sdesc_sw64(arh + o), sdesc_sw64(wrh + o), id, acc);
+          mma_f16(y1, sdesc_sw64(arh + o), sdesc_sw64(wrl + o), id, 1);
+          mma_f16(y1, sdesc_sw64(arl + o), sdesc_sw64(wrh + o), id, 1);
+          mma_f16(y2, sdesc_sw64(aih + o), sdesc_sw64(wrh + o), id, acc);
+          mma_f16(y2, sdesc_sw64(aih + o), sdesc_sw64(wrl + o), id, 1);
+          mma_f16(y2, sdesc_sw64(ail + o), sdesc_sw64(wrh + o), id, 1);
+          mma_f16(y2, sdesc_sw64(arh + o), sdesc_sw64(wih + o), id, 1);
+          mma_f16(y2, sdesc_sw64(arh + o), sdesc_sw64(wil + o), id, 1);
+          mma_f16(y2, sdesc_sw64(arl + o), sdesc_sw64(wih + o), id, 1);
+        }
+        mma_commit(&S.empty[s]);
+        if (kc == nkc - 1) mma_commit(&S.tfull);
       }
-      mma_commit(&S.empty[s]);
-      if (kc == nkc - 1) mma_commit(&S.tfull);
     }
-  } else if (warp < 4) {
-    // ------------------------------------------------------------ epilogue: d_p(tau)
-    const int row = 32 * warp + lane;
+  } else {
+    // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
+    const int quad = warp & 3, grp = warp >> 2;  // lane quadrant, column group
+    const int row = 32 * quad + lane;
     const int p = pblk * 128 + row;
-    const __half* xr_h = XT + ((size_t)k * npp + p) * ni;
-    const __half* xr_l = xr_h + xslice;
-    const __half* xi_h = xr_h + 2 * xslice;
-    const __half* xi_l = xr_h + 3 * xslice;
+    const int nblk = ni / 16;  // 16-column blocks, dealt round-robin to the 4 column groups
     const double dscale = 1.0 / ((double)kScaleA * kScaleA * kScaleW);
     for (int it = 0; it < ntau; ++it) {
       const bool ok = wait_bar(&S.tfull, it & 1, &S.abort_flag, err);
       tc_fence_after();
       float dhi = 0.f, dlo = 0.f;  // compensated (two-sum) accumulator
       if (ok) {
-        for (int n0 = 0; n0 < ni; n0 += 16) {
+        for (int bk = grp; bk < nblk; bk += 4) {
+          const int n0 = 16 * bk;
           float v1[16], v2[16];
-          tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + n0, v1);
-          tmem_ld16(tbase + ((uint32_t)(32 * warp) << 16) + ni + n0, v2);
-          const h8* a0 = reinterpret_cast<const h8*>(xr_h + n0);
-          const h8* a1 = reinterpret_cast<const h8*>(xr_l + n0);
-          const h8* b0 = reinterpret_cast<const h8*>(xi_h + n0);
-          const h8* b1 = reinterpret_cast<const h8*>(xi_l + n0);
+          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + n0, v1);
+          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + ni + n0, v2);
+          const int kc = n0 >> 5, col = n0 & 31;
           float part = 0.f;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const h8 rh = a0[h], rl = a1[h], ih = b0[h], il = b1[h];
+            const uint32_t off = sw64_off(row, col + 8 * h) / 2;
+            const h8 rh = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 0, npb, nkc) + off);
+            const h8 rl = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 1, npb, nkc) + off);
+            const h8 ih = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 2, npb, nkc) + off);
+            const h8 il = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 3, npb, nkc) + off);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float xr = __half2float(rh.v[e]) + __half2float(rl.v[e]);
@@ -456,20 +497,28 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
               part = fmaf(xi, v2[8 * h + e], part);
             }
           }
-          const float s = dhi + part;
-          const float bb = s - dhi;
-          dlo += (dhi - (s - bb)) + (part - bb);
-          dhi = s;
+          const float s2 = dhi + part;
+          const float bb = s2 - dhi;
+          dlo += (dhi - (s2 - bb)) + (part - bb);
+          dhi = s2;
         }
       }
       tc_fence_before();
       mbar_arrive(&S.tempty);
-      if (p < np) D[((size_t)k * np + p) * ntau + it] = ((double)dhi + (double)dlo) * dscale;
+      // combine the four column groups of each row
+      S.red[grp][row] = dhi + dlo;  // dlo is the two-sum error term of dhi
+      asm volatile("bar.sync 1, %0;" ::"r"(ST_EPI_WARPS * 32) : "memory");
+      if (grp == 0 && p < np) {
+        const double d = (double)S.red[0][row] + (double)S.red[1][row] + (double)S.red[2][row] +
+                         (double)S.red[3][row];
+        D[((size_t)k * np + p) * ntau + it] = d * dscale;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(ST_EPI_WARPS * 32) : "memory");
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 12) tmem_dealloc(tbase, 512);
+  if (warp == MW) tmem_dealloc(tbase, 512);
 }
 
 // Sigc_n(k|tau) += pref sum_a G_a(k-q|tau) d_(a,n)(tau); deterministic (no atomics).
@@ -509,89 +558,97 @@ int num_sms(gw_ctx* c) {
 
 gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double* P) {
   if (prec != GW_FP16X2) return set_err(c, GW_EUNSUPPORTED, "polarization: only GW_FP16X2 is built on tensor cores");
-  if (c->ntau & 1) return set_err(c, GW_EUNSUPPORTED, "polarization: ntau must be even");
-  const int nt128 = (c->ni + 127) / 128;
-  std::vector<int2> tiles;
-  std::vector<int> tile_of(nt128 * nt128, -1);
-  for (int a = 0; a < nt128; ++a)
-    for (int b = a; b < nt128; ++b) {
-      tile_of[a * nt128 + b] = (int)tiles.size();
-      tiles.push_back(make_int2(a, b));
+  const int ni = c->ni, nib = (ni + 127) / 128, nb32 = (ni + 31) / 32;
+  // strips covering the upper triangle: rows of block i, columns [128 i, ni) in pieces <= 256
+  std::vector<int4> strips;
+  std::vector<int> strip_of(nb32 * nb32, -1);
+  for (int i = 0; i < nib; ++i)
+    for (int c0 = 128 * i; c0 < ni; c0 += 256) {
+      const int N = std::min(256, ni - c0);
+      for (int ab = 4 * i; ab < std::min(4 * i + 4, nb32); ++ab)
+        for (int bb = c0 / 32; bb < (c0 + N) / 32; ++bb) strip_of[ab * nb32 + bb] = (int)strips.size();
+      strips.push_back(make_int4(i, c0, N, 0));
     }
-  const int ntiles = (int)tiles.size(), ntp = c->ntau / 2;
-  const int np = c->nb * c->nb, total = c->nk * ((np + 31) / 32), npw = (np + 31) / 32 * 32;
+  const int nstrips = (int)strips.size();
+  const int np = c->nb * c->nb, cpk = (np + 31) / 32, total = c->nk * cpk, npw = cpk * 32;
   // K segments. The tensor cores accumulate in FP32 with an error that grows with the
   // number of MMAs chained into one accumulator (measured ~2^-24 per MMA, biased), so
-  // each work unit covers at most kPolChunksPerSeg chunks of 32 pairs (128 MMA steps);
-  // the FP32 partial tiles are summed in FP64 afterwards.
+  // each work unit covers at most kPolChunksPerSeg chunks of 32 pairs (384 chained MMAs);
+  // the FP32 partial strips are summed in FP64 afterwards.
   const int sms = num_sms(c);
-  const int base_units = ntiles * ntp;
+  const int base_units = nstrips * c->ntau;
   int nseg = std::max(1, (total + kPolChunksPerSeg - 1) / kPolChunksPerSeg);
   while (base_units * nseg < 2 * sms && (total + nseg) / (nseg + 1) >= 4) ++nseg;
   const int nunits = base_units * nseg;
-  const size_t part_bytes = (size_t)nunits * 4 * 128 * 128 * sizeof(float);
+  const size_t part_bytes = (size_t)nunits * 2 * 128 * 256 * sizeof(float);
   const size_t wt_bytes = (size_t)c->nk * c->ntau * npw * sizeof(float);
+  const size_t ys_bytes = (size_t)c->nk * cpk * nib * 2 * 128 * 64 * sizeof(__half);
   gw_status st;
-  if ((st = ensure(c, &c->mw.wslices, &c->mw.wslices_bytes, part_bytes + wt_bytes, "P partials")) != GW_OK) return st;
+  if ((st = ensure(c, &c->mw.wslices, &c->mw.wslices_bytes, part_bytes + wt_bytes + ys_bytes, "P workspace")) != GW_OK)
+    return st;
   float* d_part = (float*)c->mw.wslices;
   float* d_wt = d_part + part_bytes / sizeof(float);
-  const size_t meta_bytes = sizeof(int2) * tiles.size() + sizeof(int) * tile_of.size() + sizeof(int);
-  if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P tiles")) != GW_OK) return st;
-  int2* d_tiles = reinterpret_cast<int2*>(c->mw.dacc);
-  int* d_tile_of = reinterpret_cast<int*>(d_tiles + tiles.size());
-  int* d_err = d_tile_of + tile_of.size();
-  cudaMemcpyAsync(d_tiles, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(d_tile_of, tile_of.data(), sizeof(int) * tile_of.size(), cudaMemcpyHostToDevice, c->stream);
+  __half* d_ys = (__half*)((char*)d_wt + wt_bytes);
+  const size_t meta_bytes = sizeof(int4) * strips.size() + sizeof(int) * strip_of.size() + sizeof(int);
+  if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P strips")) != GW_OK) return st;
+  int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
+  int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
+  int* d_err = d_strip_of + strip_of.size();
+  cudaMemcpyAsync(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice, c->stream);
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
-  const size_t smem = 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem);
-  cudaFuncSetAttribute(k_pol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
+  if (ni % 128) cudaMemsetAsync(d_ys, 0, ys_bytes, c->stream);  // rows >= ni of the last block stay zero
+  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * ni * np;
+  const int64_t nsp = (int64_t)c->nk * ni * cpk * 4;
+  k_split_y<<<(unsigned)((nsp + 255) / 256), 256, 0, c->stream>>>(Mq, c->nk, ni, np, cpk, nib, d_ys);
+  if ((st = check_launch(c, "split_y")) != GW_OK) return st;
   const int64_t nwt = (int64_t)c->nk * c->ntau * npw;
   k_pol_weights<<<(unsigned)((nwt + 255) / 256), 256, 0, c->stream>>>(G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->nb,
                                                                       c->ntau, npw, d_wt);
   if ((st = check_launch(c, "pol_weights")) != GW_OK) return st;
-  k_pol_tc<<<nunits, PT_THREADS, smem, c->stream>>>(Mq, d_wt, c->nk, c->ni, c->nb, c->ntau, npw, ntiles, d_tiles, nseg,
+  const size_t smem = 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem);
+  cudaFuncSetAttribute(k_pol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_pol_tc<<<nunits, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips, d_strips, nseg,
                                                     d_part, d_err);
   if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
-  const int64_t tot = (int64_t)c->ntau * c->ni * c->ni;
   const double scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
-  k_pol_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(d_part, c->ni, c->ntau, nt128,
-                                                                     d_tile_of, ntiles, nseg, scale, (double2*)P);
+  k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
+                                                                           d_strips, nseg, scale, (double2*)P);
   return check_launch(c, "pol_reduce");
 }
 
 gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W, int prec, double* S) {
   if (prec != GW_FP16X2) return set_err(c, GW_EUNSUPPORTED, "self-energy: only GW_FP16X2 is built on tensor cores");
   if (c->ni > 256) return set_err(c, GW_EUNSUPPORTED, "tensor-core self-energy: ni <= 256");
-  const int np = c->nb * c->nb, npp = (np + 127) / 128 * 128;
+  const int np = c->nb * c->nb, npb = (np + 127) / 128, npp = npb * 128;
   const size_t xbytes = (size_t)4 * c->nk * npp * c->ni * sizeof(__half);
   const size_t wbytes = (size_t)4 * c->ntau * c->ni * c->ni * sizeof(__half);
   const size_t dbytes = (size_t)c->nk * np * c->ntau * sizeof(double);
   gw_status st;
-  if ((st = ensure(c, &c->mw.mslices, &c->mw.mslices_bytes, xbytes + wbytes + dbytes + sizeof(int), "Sigma slices")) !=
+  if ((st = ensure(c, &c->mw.mslices, &c->mw.mslices_bytes, xbytes + wbytes + dbytes + 256, "Sigma slices")) !=
       GW_OK)
     return st;
-  __half* XT = (__half*)c->mw.mslices;
-  __half* BW = XT + xbytes / sizeof(__half);
+  __half* XS = (__half*)c->mw.mslices;
+  __half* WS = XS + xbytes / sizeof(__half);
   double* D = (double*)((char*)c->mw.mslices + xbytes + wbytes);
   int* d_err = (int*)((char*)D + dbytes);
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
   if (c->mw.iq != iq || c->mw.prec != prec) {
-    dim3 g((npp + 31) / 32, (c->ni + 31) / 32, c->nk);
-    k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->nk, c->ni, np, npp, XT);
+    dim3 g(npp / 32, (c->ni + 31) / 32, c->nk);
+    k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->ni, np, npb, XS);
     if ((st = check_launch(c, "split_x")) != GW_OK) return st;
     c->mw.iq = iq;
     c->mw.prec = prec;
   }
   const int64_t nw = (int64_t)c->ntau * c->ni * c->ni;
-  k_split_w<<<(unsigned)((nw + 255) / 256), 256, 0, c->stream>>>((const double2*)W, c->ntau, c->ni, BW);
+  k_split_w<<<(unsigned)((nw + 255) / 256), 256, 0, c->stream>>>((const double2*)W, c->ntau, c->ni, WS);
   if ((st = check_launch(c, "split_w")) != GW_OK) return st;
   const int stage_bytes = 4 * S_ATILE + 4 * c->ni * 64;
   const size_t smem = 1024 + 2 * stage_bytes + sizeof(SigSmem);
   cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  dim3 grid(npp / 128, c->nk);
-  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XT, BW, c->nk, c->ni, npp, c->ntau, D, np, d_err);
+  dim3 grid(npb, c->nk);
+  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, WS, c->ni, npb, c->ntau, D, np, d_err);
   if ((st = check_launch(c, "sig_tc")) != GW_OK) return st;
   const int64_t n = (int64_t)c->nk * c->nb * c->ntau;
   k_sig_reduce<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(D, G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->nb,
