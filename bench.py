@@ -183,12 +183,16 @@ def main():
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="fp16x2", choices=["fp16x2", "fp64"])
     ap.add_argument("--config", default="c2")
-    ap.add_argument("--omega", type=float, default=1.0)
+    ap.add_argument("--omega", type=float, default=None,
+                    help="unit-cell volume in 1/(Omega Nk); default: the paper's Si cell, 270.1 bohr^3")
     ap.add_argument("--nq", type=int, default=0, help="limit q points (profiling / exploration only; not a bench line)")
     ap.add_argument("--nk", type=int, default=0, help="override Nk (profiling small cases only; not a bench line)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.omega is None:
+        import gwinputs as gi
+        args.omega = gi.OMEGA_SI
     if args.impl == "reference":
         return run_reference(args, args.config)
 

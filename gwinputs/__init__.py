@@ -322,6 +322,10 @@ def make_grid(beta, ntau, nnu, nw, ncont=128, tau_min=1e-3, lam=None, tol=1e-10)
                 w_idx=w_idx, ncont=int(ncont))
 
 
+# Unit-cell volume Omega of 1/(Omega N_k) (Eqs. irpol, sigc): the paper's silicon cell,
+# a = 5.43 Angstrom (Sec. IV), primitive fcc volume a^3 / 4 in bohr^3.
+OMEGA_SI = (5.43 / 0.529177210903) ** 3 / 4.0
+
 # ---------------------------------------------------------------------------
 # Workload configurations (synthetic stand-ins for the paper's crystals)
 # ---------------------------------------------------------------------------

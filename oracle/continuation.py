@@ -10,8 +10,8 @@ loops (test infrastructure; see the package docstring).
   with h_m the hat function at node x_m. The b are the non-negative
   least-squares minimisers of sum_n |Sigma~(i w_n) - Sigma(i w_n)|^2
   (Lawson-Hanson NNLS via SciPy).
-* QP: root of E - eps - Sigma^x + Sigma_0 - Re Sigma^c(E) = 0 nearest eps
-  (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where this vanishes).
+* QP: root of E - eps - Sigma^x + Sigma_0 - Re Sigma^c(E) = 0 nearest eps with positive
+  quasiparticle weight (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where this vanishes).
 """
 from __future__ import annotations
 
@@ -107,23 +107,51 @@ def cpe_resig(b, x):
 
 
 # ---------------------------------------------------------------- QP
+QP_SCAN = 401        # scan points on [eps - 1, eps + 1] Ha
+QP_STEP = 0.005      # Ha
+QP_BISECT = 60
+
+
 def qp_solve(eps, sigx, vxc, resig, de=1e-6, tol=1e-12, maxit=100):
-    """Quasiparticle energy: root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E)
-    nearest eps by secant/Newton iteration from E = eps (resig(E) returns
-    Re Sigma^c at real E). Returns (E, Z, ok)."""
-    E = float(eps)
-    ok = False
-    for _ in range(maxit):
-        F = E - eps - sigx + vxc - resig(E)
-        dF = 1.0 - (resig(E + de) - resig(E - de)) / (2 * de)
-        if dF == 0 or not np.isfinite(dF):
-            break
-        step = F / dF
-        step = max(-0.5, min(0.5, step))
-        E -= step
-        if abs(step) < tol * max(1.0, abs(E)):
-            ok = True
-            break
+    """Quasiparticle energy: root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E) nearest eps
+    (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where F vanishes).
+
+    F is scanned on E_j = eps + (j - 200) 0.005 Ha, j = 0..400; among the upward crossings
+    F_j < 0 <= F_{j+1} (quasiparticle weight Z > 0) the one whose midpoint is nearest eps is
+    refined by 60 bisections. Without a crossing, Newton iteration from eps (central-difference
+    derivative, steps clamped to 0.5 Ha) is the fallback. Returns (E, Z, ok) with ok False for
+    the fallback or a Newton failure."""
+    F = lambda E: E - eps - sigx + vxc - resig(E)  # noqa: E731
+    Es = [eps + (j - (QP_SCAN // 2)) * QP_STEP for j in range(QP_SCAN)]
+    Fs = [F(E) for E in Es]
+    best = None
+    for j in range(QP_SCAN - 1):
+        if Fs[j] < 0.0 <= Fs[j + 1]:
+            d = abs(0.5 * (Es[j] + Es[j + 1]) - eps)
+            if best is None or d < best[0]:
+                best = (d, j)
+    if best is not None:
+        lo, hi = Es[best[1]], Es[best[1] + 1]
+        for _ in range(QP_BISECT):
+            mid = 0.5 * (lo + hi)
+            if F(mid) < 0.0:
+                lo = mid
+            else:
+                hi = mid
+        E = 0.5 * (lo + hi)
+        ok = True
+    else:
+        E = float(eps)
+        ok = False
+        for _ in range(maxit):
+            Fv = F(E)
+            dF = 1.0 - (resig(E + de) - resig(E - de)) / (2 * de)
+            if dF == 0 or not np.isfinite(dF):
+                break
+            step = max(-0.5, min(0.5, Fv / dF))
+            E -= step
+            if abs(step) < tol * max(1.0, abs(E)):
+                break
     dS = (resig(E + de) - resig(E - de)) / (2 * de)
     return E, 1.0 / (1.0 - dS), ok
 

@@ -4,8 +4,8 @@
 //          on a real grid, Sigma(z) = sum_m b_m Phi_m(z), b_m >= 0 (causality, Im Sigma <= 0),
 //          Phi_m(z) = int hat_m(x) / (z - x) dx; b from Lawson-Hanson NNLS on the normal
 //          equations of the ridge-regularised fit (one thread block per problem).
-//  * QP  : Newton iteration on F(E) = E - eps - sigx + vxc - Re Sigma^c(E + i eta) from E = eps
-//          (central-difference derivative, step clamped to 0.5 Ha), eta = 1e-4 Ha.
+//  * QP  : root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E + i eta), eta = 1e-4 Ha: the
+//          upward crossing nearest eps on a 0.005 Ha scan of eps +- 1 Ha, refined by bisection.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,32 +53,76 @@ __device__ cd cpe_phi(const double* x, int m, cd z) {
 
 __device__ double resig_pade(const cd* a, int n, double beta, double E) { return pade_eval(a, n, beta, {E, kEta}).x; }
 
+// Re sum_m b_m Phi_m(E + i eta); the node logarithms are shared between neighbouring hats.
 __device__ double resig_cpe(const double* b, const double* x, int ng, double E) {
+  const cd z = {E, kEta};
   double s = 0.0;
-  for (int m = 0; m < ng; ++m)
-    if (b[m] != 0.0) s += b[m] * cpe_phi(x, m, {E, kEta}).x;
+  cd l0 = clog_(csub(z, cd{x[0], 0.0})), l1 = clog_(csub(z, cd{x[1], 0.0}));
+  for (int m = 0; m < ng; ++m) {
+    const cd l2 = clog_(csub(z, cd{x[m + 2], 0.0}));
+    if (b[m] != 0.0) {
+      const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
+      const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
+      const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
+      s += b[m] * (rise.x + fall.x);
+    }
+    l0 = l1;
+    l1 = l2;
+  }
   return s;
 }
 
+// QP root nearest eps with an upward crossing of F(E) = E - eps - sx + vxc - Re Sigma^c(E):
+// scan E_j = eps + (j - 200) 0.005 Ha (j = 0..400), refine the crossing nearest eps by 60
+// bisections; without a crossing fall back to Newton from eps (ok = 0).
+constexpr int kQpScan = 401;
+constexpr double kQpStep = 0.005;
+
 template <class F>
-__device__ void qp_newton(F resig, double eps, double sx, double vxc, double* E_out, int* ok_out) {
+__device__ void qp_solve(F resig, double eps, double sx, double vxc, double* E_out, int* ok_out) {
+  auto Ff = [&](double E) { return E - eps - sx + vxc - resig(E); };
+  int best = -1;
+  double bestd = 0.0;
+  double Fprev = Ff(eps - (kQpScan / 2) * kQpStep);
+  for (int j = 0; j < kQpScan - 1; ++j) {
+    const double E1 = eps + (j + 1 - kQpScan / 2) * kQpStep;
+    const double F1 = Ff(E1);
+    if (Fprev < 0.0 && F1 >= 0.0) {
+      const double E0 = eps + (j - kQpScan / 2) * kQpStep;
+      const double d = fabs(0.5 * (E0 + E1) - eps);
+      if (best < 0 || d < bestd) {
+        best = j;
+        bestd = d;
+      }
+    }
+    Fprev = F1;
+  }
+  if (best >= 0) {
+    double lo = eps + (best - kQpScan / 2) * kQpStep, hi = eps + (best + 1 - kQpScan / 2) * kQpStep;
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (Ff(mid) < 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    *E_out = 0.5 * (lo + hi);
+    *ok_out = 1;
+    return;
+  }
   double E = eps;
   const double de = 1e-6;
-  int ok = 0;
   for (int it = 0; it < 100; ++it) {
-    const double Fv = E - eps - sx + vxc - resig(E);
+    const double Fv = Ff(E);
     const double dF = 1.0 - (resig(E + de) - resig(E - de)) / (2.0 * de);
     if (dF == 0.0 || !isfinite(dF)) break;
     double step = Fv / dF;
     step = fmax(-0.5, fmin(0.5, step));
     E -= step;
-    if (fabs(step) < 1e-12 * fmax(1.0, fabs(E))) {
-      ok = 1;
-      break;
-    }
+    if (fabs(step) < 1e-12 * fmax(1.0, fabs(E))) break;
   }
   *E_out = E;
-  *ok_out = ok;
+  *ok_out = 0;
 }
 
 // One thread per problem: coefficients, real-axis values, QP root.
@@ -109,7 +153,7 @@ __global__ void k_pade(int64_t nprob, const double2* __restrict__ sig, int ncont
   }
   double E;
   int ok;
-  qp_newton([&](double e) { return resig_pade(a, npade, beta, e); }, eps[p], sigx[p], vxc[p], &E, &ok);
+  qp_solve([&](double e) { return resig_pade(a, npade, beta, e); }, eps[p], sigx[p], vxc[p], &E, &ok);
   eqp[p] = E;
   info[p] = ok ? 0 : 1;
 }
@@ -279,7 +323,7 @@ __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const doub
   }
   double E;
   int ok;
-  qp_newton([&](double e) { return resig_cpe(bp, x, ng, e); }, eps[p], sigx[p], vxc[p], &E, &ok);
+  qp_solve([&](double e) { return resig_cpe(bp, x, ng, e); }, eps[p], sigx[p], vxc[p], &E, &ok);
   eqp[p] = E;
   if (info[p] == 0 && !ok) info[p] = 1;
 }

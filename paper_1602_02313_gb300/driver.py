@@ -13,8 +13,18 @@ from __future__ import annotations
 
 import torch
 
-from . import (GW_BOSE, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
+from . import (GW_BOSE, GW_CPE, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
                GW_TAU_TO_IW_CONT, GwError)
+
+
+def cpe_grid(nhat=128, xmin=0.01, xmax=50.0):
+    """Real-frequency nodes of the continuous-pole expansion: +-geomspace(xmin, xmax, nhat/2)
+    and two end nodes where the hats vanish (same construction as the oracle's)."""
+    import numpy as np
+    h = nhat // 2
+    g = np.geomspace(xmin, xmax, h)
+    r = g[1] / g[0]
+    return np.concatenate([[-xmax * r], -g[::-1], g, [xmax * r]])
 
 
 def contraction_flops(nk, nb, ni, ntau):
@@ -28,7 +38,7 @@ def contraction_flops(nk, nb, ni, ntau):
 class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
-    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE):
+    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-5):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
@@ -58,6 +68,9 @@ class Chain:
         self.qinfo = torch.zeros(nk * nb, dtype=torch.int32, **d)
         self.vxc = None
         self.timers = None
+        if cont_method == GW_CPE:
+            self.cpe_x = cpe_grid()
+            ctx.cpe_setup(self.cpe_x, cpe_ridge)
 
     def _timed(self, key, fn):
         if self.timers is None:

@@ -116,3 +116,34 @@ def test_c2_full_size_tc_vs_fp64(gw):
     e = rel(host(S16), host(S64))
     print(f"c2: Sigma tensor-core vs FP64 rel err {e:.3e}")
     assert e < TOL_S
+
+
+def test_chain_qp_gap_mixed_vs_fp64(gw):
+    """Whole G0W0 chain (all q) with c2 shapes at Nk = 8 and the paper's silicon cell volume:
+    quasiparticle energies and the band gap from the tensor-core path against the FP64 path,
+    with Pade and with CPE continuation. Reported with the |Sigma| scale it was measured at."""
+    from paper_1602_02313_gb300.driver import Chain
+    cr, gr = gi.make_config("c2", nk=8)
+    res = {}
+    for name, prec in [("fp64", gw.GW_FP64), ("fp16x2", gw.GW_FP16X2)]:
+        for cont in (gw.GW_PADE, gw.GW_CPE):
+            ctx = gw.GW(gr, cr, omega=gi.OMEGA_SI)
+            ch = Chain(ctx, dev(cr.eps), prec=prec, qb=4, cont_method=cont)
+            ch.step()
+            ch.check()
+            res[(name, cont)] = {"eqp": host(ch.eqp).reshape(cr.nk, cr.nb), "sx": host(ch.Sx), "S": host(ch.S),
+                                 "ok": host(ch.qinfo) == 0}
+            ctx.close()
+    gap = lambda E: E[:, cr.nocc].min() - E[:, cr.nocc - 1].max()  # noqa: E731
+    ha2mev = 27211.386
+    for cont, cname in [(gw.GW_PADE, "pade"), (gw.GW_CPE, "cpe")]:
+        a, b = res[("fp64", cont)], res[("fp16x2", cont)]
+        dE = np.abs(a["eqp"] - b["eqp"]).max()
+        dgap = abs(gap(a["eqp"]) - gap(b["eqp"]))
+        eS = rel(b["S"], a["S"])
+        print(f"chain nk=8 {cname}: |Sigma^x| {np.abs(a['sx']).max():.3e} Ha, |Sigma^c(tau)| {np.abs(a['S']).max():.3e} Ha;"
+              f" Sigma^c rel err {eS:.3e}; max |dE_qp| {dE * ha2mev:.4f} meV; gap fp64 {gap(a['eqp']):.6f} Ha,"
+              f" |dgap| {dgap * ha2mev:.4f} meV; QP roots found {a['ok'].mean():.3f}")
+        assert eS < 1e-3
+    a, b = res[("fp64", gw.GW_CPE)], res[("fp16x2", gw.GW_CPE)]
+    assert abs(gap(a["eqp"]) - gap(b["eqp"])) * ha2mev < 1.0  # the 1 meV target, CPE continuation
