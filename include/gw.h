@@ -191,6 +191,50 @@ gw_status gw_cpe_setup(gw_ctx* ctx, int ngrid, const double* x, double ridge);
 /* CPE coefficients of the last gw_continue(GW_CPE) call: b out [nprob][ngrid]. */
 gw_status gw_cpe_coeffs(gw_ctx* ctx, double* b);
 
+/* ---------------------------------------------------------------------------------------
+ * Learned seed of the continuous-pole expansion (not in the paper). A multilayer perceptron
+ * maps the normalised Matsubara self-energy of one (k, n) problem to non-negative pole weights
+ * on the CPE grid; the weights warm-start the Lawson-Hanson fit of gw_continue(GW_CPE).
+ * Training is unsupervised: L = (1/B) sum_b ||A b_hat_b - x_b||^2 with A the real-stacked CPE
+ * kernel at the first nfit fermionic frequencies (gw_cpe_fit_matrix). All products run on the
+ * tensor cores (fp16 operands, FP32 accumulation); weights are FP32 with fp16 copies.
+ * ------------------------------------------------------------------------------------- */
+typedef struct gw_mlp gw_mlp;
+
+/* Network nin -> nh (nhidden GELU layers) -> nout (softplus). nin % 64 == 0, nh and nout % 128 == 0.
+ * Weights drawn from a seeded generator; ordered on the cudaStream_t `stream`. */
+gw_status gw_mlp_create(gw_mlp** mlp, int nin, int nh, int nhidden, int nout, uint64_t seed, int device,
+                        void* stream);
+gw_status gw_mlp_destroy(gw_mlp* mlp);
+const char* gw_mlp_last_error(gw_mlp* mlp);
+/* Number of parameters (per layer: W [out][in] row-major, then b [out]). */
+int64_t gw_mlp_num_params(gw_mlp* mlp);
+/* x (device) float [batch][nin] -> out (device) float [batch][nout]; batch % 128 == 0. */
+gw_status gw_mlp_forward(gw_mlp* mlp, int64_t batch, const float* x, float* out);
+/* Loss and gradients at the current weights (no update). x float [batch][nin] with nin = nx;
+ * Acpe float [nx][nout]; loss (device, may be NULL) float [1]; grads (device, may be NULL)
+ * float [num_params] in parameter order. */
+gw_status gw_mlp_loss_grad(gw_mlp* mlp, int64_t batch, const float* x, int nx, const float* Acpe, float* loss,
+                           float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss as above. */
+gw_status gw_mlp_train_step(gw_mlp* mlp, int64_t batch, const float* x, int nx, const float* Acpe, float lr,
+                            float* loss);
+/* Host copies of the FP32 parameters in parameter order (float [num_params]). */
+gw_status gw_mlp_get_params(gw_mlp* mlp, float* params);
+gw_status gw_mlp_set_params(gw_mlp* mlp, const float* params);
+
+/* Network input from Sigma^c(i w): x float [nprob][2 nfit] = [Re, Im of the first nfit dense
+ * frequencies] / scale, scale double [nprob] = max |component| (device arrays). */
+gw_status gw_cpe_features(gw_ctx* ctx, int64_t nprob, const double* sig_iw, int nfit, float* x, double* scale);
+/* A float [2 nfit][ngrid] (device): the CPE kernel at the first nfit dense frequencies (after gw_cpe_setup). */
+gw_status gw_cpe_fit_matrix(gw_ctx* ctx, int nfit, float* A);
+/* Warm start of the next gw_continue(GW_CPE) call with the same nprob: b0 = scale * bhat
+ * (bhat float [nprob][ngrid], scale double [nprob], device). The active set starts at the
+ * support of b0. Consumed by that call. */
+gw_status gw_cpe_seed(gw_ctx* ctx, int64_t nprob, const float* bhat, const double* scale);
+/* Lawson-Hanson outer iterations of the last gw_continue(GW_CPE) call: iters (device) int [nprob]. */
+gw_status gw_cpe_iterations(gw_ctx* ctx, int* iters);
+
 /* Matrix elements the context uses (for inspection and tests): copies
  * M[iq][k][:][:][:] for k in [k0, k0 + nk_copy) into out cplx [nk_copy][ni][nb][nb]. */
 gw_status gw_copy_m(gw_ctx* ctx, int iq, int k0, int nk_copy, double* out);

@@ -30,5 +30,6 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401
+from . import mlp  # noqa: F401
 from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
                            cpe_eval, qp_solve, band_gap, pade_resig, cpe_resig, ETA)

@@ -33,7 +33,9 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
-           "gw_screen_static"]
+           "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
+           "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_get_params", "gw_mlp_set_params",
+           "gw_cpe_features", "gw_cpe_fit_matrix", "gw_cpe_seed", "gw_cpe_iterations"]
 
 
 class GwError(RuntimeError):
@@ -108,11 +110,22 @@ def load_library(path=LIB_PATH):
         "gw_transform_matrices": [ctypes.POINTER(_Grid), vp, vp, vp, vp, vp],
         "gw_launch_count": [vp],
         "gw_screen_static": [i32, i32, i32, vp, vp, vp, vp, vp],
+        "gw_mlp_create": [ctypes.POINTER(vp), i32, i32, i32, i32, ctypes.c_uint64, i32, vp],
+        "gw_mlp_destroy": [vp], "gw_mlp_last_error": [vp], "gw_mlp_num_params": [vp],
+        "gw_mlp_forward": [vp, i64, vp, vp],
+        "gw_mlp_loss_grad": [vp, i64, vp, i32, vp, vp, vp],
+        "gw_mlp_train_step": [vp, i64, vp, i32, vp, ctypes.c_float, vp],
+        "gw_mlp_get_params": [vp, vp], "gw_mlp_set_params": [vp, vp],
+        "gw_cpe_features": [vp, i64, vp, i32, vp, vp],
+        "gw_cpe_fit_matrix": [vp, i32, vp],
+        "gw_cpe_seed": [vp, i64, vp, vp],
+        "gw_cpe_iterations": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = {"gw_last_error": ctypes.c_char_p, "gw_launch_count": ctypes.c_int64}.get(name, ctypes.c_int)
+        f.restype = {"gw_last_error": ctypes.c_char_p, "gw_mlp_last_error": ctypes.c_char_p,
+                     "gw_launch_count": ctypes.c_int64, "gw_mlp_num_params": ctypes.c_int64}.get(name, ctypes.c_int)
     return lib
 
 
@@ -230,3 +243,72 @@ class GW:
 
     def copy_m(self, iq, k0, nkc, out):
         self._check(self.lib.gw_copy_m(self.h, iq, k0, nkc, _ptr(out)), "gw_copy_m")
+
+    # ------------------------------------------------------------------ learned CPE seed
+    def cpe_features(self, sig_iw, nfit, x, scale):
+        self._check(self.lib.gw_cpe_features(self.h, scale.numel(), _ptr(sig_iw), int(nfit), _ptr(x), _ptr(scale)),
+                    "gw_cpe_features")
+
+    def cpe_fit_matrix(self, nfit, A):
+        self._check(self.lib.gw_cpe_fit_matrix(self.h, int(nfit), _ptr(A)), "gw_cpe_fit_matrix")
+
+    def cpe_seed(self, bhat, scale):
+        self._check(self.lib.gw_cpe_seed(self.h, scale.numel(), _ptr(bhat), _ptr(scale)), "gw_cpe_seed")
+
+    def cpe_iterations(self, iters):
+        self._check(self.lib.gw_cpe_iterations(self.h, _ptr(iters)), "gw_cpe_iterations")
+
+
+class MLP:
+    """gw_mlp handle: the learned CPE seed network (tensor-core forward / backward / Adam)."""
+
+    def __init__(self, nin=128, nh=256, nhidden=3, nout=128, seed=1, device=0, stream=None):
+        import torch
+        self.lib = lib()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        st = self.lib.gw_mlp_create(ctypes.byref(h), nin, nh, nhidden, nout, seed, device,
+                                    ctypes.c_void_p(self.stream.cuda_stream))
+        if st != GW_OK:
+            raise GwError(f"gw_mlp_create failed: {_STATUS.get(st, st)}")
+        self.h = h
+        self.nin, self.nout = nin, nout
+
+    def _check(self, st, what):
+        if st != GW_OK:
+            msg = self.lib.gw_mlp_last_error(self.h)
+            raise GwError(f"{what}: {_STATUS.get(st, st)}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gw_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self):
+        return int(self.lib.gw_mlp_num_params(self.h))
+
+    def forward(self, x, out):
+        self._check(self.lib.gw_mlp_forward(self.h, x.shape[0], _ptr(x), _ptr(out)), "gw_mlp_forward")
+
+    def loss_grad(self, x, A, loss=None, grads=None):
+        self._check(self.lib.gw_mlp_loss_grad(self.h, x.shape[0], _ptr(x), x.shape[1], _ptr(A), _ptr(loss),
+                                              _ptr(grads)), "gw_mlp_loss_grad")
+
+    def train_step(self, x, A, lr, loss=None):
+        self._check(self.lib.gw_mlp_train_step(self.h, x.shape[0], _ptr(x), x.shape[1], _ptr(A), float(lr),
+                                               _ptr(loss)), "gw_mlp_train_step")
+
+    def get_params(self):
+        p = np.zeros(self.num_params(), np.float32)
+        self._check(self.lib.gw_mlp_get_params(self.h, ctypes.c_void_p(p.ctypes.data)), "gw_mlp_get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        self._check(self.lib.gw_mlp_set_params(self.h, ctypes.c_void_p(p.ctypes.data)), "gw_mlp_set_params")

@@ -165,7 +165,7 @@ constexpr int kCpeMaxGrid = 128;
 __global__ void __launch_bounds__(128) k_cpe_nnls(int64_t nprob, const double2* __restrict__ sig, int ncont,
                                                   const double* __restrict__ A, const double* __restrict__ N, int ng,
                                                   const double* __restrict__ b0, double* __restrict__ bout,
-                                                  int* __restrict__ info) {
+                                                  int* __restrict__ info, int* __restrict__ iters) {
   extern __shared__ double L[];  // [kCpeMaxGrid][kCpeMaxGrid], dynamic
   __shared__ double cvec[kCpeMaxGrid], x[kCpeMaxGrid], z[kCpeMaxGrid], w[kCpeMaxGrid];
   __shared__ int Pset[kCpeMaxGrid], idx[kCpeMaxGrid];
@@ -301,7 +301,10 @@ __global__ void __launch_bounds__(128) k_cpe_nnls(int64_t nprob, const double2* 
     }
   }
   for (int m = t; m < ng; m += blockDim.x) bout[(size_t)prob * ng + m] = x[m];
-  if (t == 0) info[prob] = status;
+  if (t == 0) {
+    info[prob] = status;
+    if (iters) iters[prob] = outer;
+  }
 }
 
 __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const double* __restrict__ x, int ng,
@@ -354,8 +357,21 @@ gw_status launch_continue(gw_ctx* c, int method, int64_t nprob, const double* si
   const size_t smem = sizeof(double) * kCpeMaxGrid * kCpeMaxGrid;
   cudaFuncSetAttribute(k_cpe_nnls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c->cpe_nprob = nprob;
+  if ((size_t)nprob * sizeof(int) > c->cpe_iters_bytes) {
+    if (c->d_cpe_iters) cudaFree(c->d_cpe_iters);
+    c->d_cpe_iters = nullptr;
+    c->cpe_iters_bytes = 0;
+    if (cudaMalloc((void**)&c->d_cpe_iters, nprob * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, GW_ENOMEM, "cpe iteration counts");
+    }
+    c->cpe_iters_bytes = nprob * sizeof(int);
+  }
+  const double* seed = nullptr;
+  if (c->cpe_seed_nprob == nprob) seed = c->d_cpe_seed;  // a seed set by gw_cpe_seed, consumed once
+  c->cpe_seed_nprob = 0;
   k_cpe_nnls<<<(unsigned)nprob, 128, smem, c->stream>>>(nprob, (const double2*)sig_iw, c->ncont, c->d_cpe_A, c->d_cpe_N,
-                                                     c->cpe_ngrid, nullptr, c->d_cpe_b, info);
+                                                     c->cpe_ngrid, seed, c->d_cpe_b, info, c->d_cpe_iters);
   gw_status s = check_launch(c, "cpe_nnls");
   if (s != GW_OK) return s;
   k_cpe_qp<<<(unsigned)((nprob + 63) / 64), 64, 0, c->stream>>>(nprob, c->d_cpe_b, c->d_cpe_x, c->cpe_ngrid, eps,
@@ -418,5 +434,85 @@ extern "C" gw_status gw_cpe_coeffs(gw_ctx* c, double* b) {
   const size_t bytes = (size_t)c->cpe_nprob * c->cpe_ngrid * sizeof(double);
   if (cudaMemcpyAsync(b, c->d_cpe_b, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
     return set_err(c, GW_ECUDA, "gw_cpe_coeffs");
+  return GW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Learned-seed support (not in the paper): features and fit matrix for the MLP,
+// and the warm start of the next GW_CPE call.
+// ---------------------------------------------------------------------------
+namespace gwi {
+namespace seedk {
+// x[p] = [Re s_p(i w_0..nfit-1), Im s_p(...)] / scale_p, scale_p = max |component| (1 if zero)
+__global__ void k_cpe_features(int64_t nprob, const double2* __restrict__ sig, int ncont, int nfit,
+                               float* __restrict__ x, double* __restrict__ scale) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const double2* s = sig + (size_t)p * ncont;
+  double mx = 0.0;
+  for (int n = 0; n < nfit; ++n) mx = fmax(mx, fmax(fabs(s[n].x), fabs(s[n].y)));
+  const double sc = mx > 0.0 ? mx : 1.0;
+  for (int n = 0; n < nfit; ++n) {
+    x[(size_t)p * 2 * nfit + n] = (float)(s[n].x / sc);
+    x[(size_t)p * 2 * nfit + nfit + n] = (float)(s[n].y / sc);
+  }
+  scale[p] = sc;
+}
+__global__ void k_cpe_fitmat(const double* __restrict__ A, int ncont, int ng, int nfit, float* __restrict__ out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * nfit * ng) return;
+  const int r = e / ng, m = e % ng;
+  const int src = r < nfit ? r : ncont + (r - nfit);
+  out[e] = (float)A[(size_t)src * ng + m];
+}
+__global__ void k_cpe_seed(int64_t n, int ng, const float* __restrict__ bhat, const double* __restrict__ scale,
+                           double* __restrict__ b0) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  b0[e] = (double)bhat[e] * scale[e / ng];
+}
+}  // namespace seedk
+}  // namespace gwi
+using namespace gwi::seedk;
+
+extern "C" gw_status gw_cpe_features(gw_ctx* c, int64_t nprob, const double* sig_iw, int nfit, float* x,
+                                     double* scale) {
+  if (!c || nprob <= 0 || !sig_iw || !x || !scale || nfit < 1 || nfit > c->ncont) return GW_EINVAL;
+  k_cpe_features<<<(unsigned)((nprob + 127) / 128), 128, 0, c->stream>>>(nprob, (const double2*)sig_iw, c->ncont,
+                                                                         nfit, x, scale);
+  return check_launch(c, "cpe_features");
+}
+
+extern "C" gw_status gw_cpe_fit_matrix(gw_ctx* c, int nfit, float* A) {
+  if (!c || !A || c->cpe_ngrid == 0 || nfit < 1 || nfit > c->ncont) return GW_EINVAL;
+  const int n = 2 * nfit * c->cpe_ngrid;
+  k_cpe_fitmat<<<(n + 255) / 256, 256, 0, c->stream>>>(c->d_cpe_A, c->ncont, c->cpe_ngrid, nfit, A);
+  return check_launch(c, "cpe_fit_matrix");
+}
+
+extern "C" gw_status gw_cpe_seed(gw_ctx* c, int64_t nprob, const float* bhat, const double* scale) {
+  if (!c || nprob <= 0 || !bhat || !scale || c->cpe_ngrid == 0) return GW_EINVAL;
+  const size_t need = (size_t)nprob * c->cpe_ngrid * sizeof(double);
+  if (need > c->cpe_seed_bytes) {
+    if (c->d_cpe_seed) cudaFree(c->d_cpe_seed);
+    c->d_cpe_seed = nullptr;
+    c->cpe_seed_bytes = 0;
+    if (cudaMalloc((void**)&c->d_cpe_seed, need) != cudaSuccess) {
+      cudaGetLastError();
+      return set_err(c, GW_ENOMEM, "cpe seed");
+    }
+    c->cpe_seed_bytes = need;
+  }
+  const int64_t n = nprob * c->cpe_ngrid;
+  k_cpe_seed<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(n, c->cpe_ngrid, bhat, scale, c->d_cpe_seed);
+  c->cpe_seed_nprob = nprob;
+  return check_launch(c, "cpe_seed");
+}
+
+extern "C" gw_status gw_cpe_iterations(gw_ctx* c, int* iters) {
+  if (!c || !iters || !c->d_cpe_iters || c->cpe_nprob <= 0) return GW_EINVAL;
+  if (cudaMemcpyAsync(iters, c->d_cpe_iters, c->cpe_nprob * sizeof(int), cudaMemcpyDeviceToDevice, c->stream) !=
+      cudaSuccess)
+    return set_err(c, GW_ECUDA, "gw_cpe_iterations");
   return GW_OK;
 }

@@ -483,6 +483,8 @@ gw_status gw_destroy(gw_ctx* c) {
   for (double* p : bufs)
     if (p) cudaFree(p);
   if (c->d_kmq) cudaFree(c->d_kmq);
+  if (c->d_cpe_iters) cudaFree(c->d_cpe_iters);
+  if (c->d_cpe_seed) cudaFree(c->d_cpe_seed);
   if (c->d_widx) cudaFree(c->d_widx);
   if (c->d_tau) cudaFree(c->d_tau);
   free_mixed(c);

@@ -89,6 +89,11 @@ struct gw_ctx {
   double* d_cpe_b = nullptr;    // [nprob][ngrid]
   size_t cpe_b_bytes = 0;
   int64_t cpe_nprob = 0;       // problems of the last GW_CPE call
+  int* d_cpe_iters = nullptr;   // [nprob] Lawson-Hanson outer iterations of the last call
+  size_t cpe_iters_bytes = 0;
+  double* d_cpe_seed = nullptr; // [nprob][ngrid] warm start for the next GW_CPE call
+  size_t cpe_seed_bytes = 0;
+  int64_t cpe_seed_nprob = 0;
   double* d_pade = nullptr;     // cplx [nprob][npade] coefficients
   size_t pade_bytes = 0;
   // tensor-core path

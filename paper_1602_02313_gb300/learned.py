@@ -1,0 +1,73 @@
+"""Learned seed of the continuous-pole expansion (not in the paper): training data from
+G0W0 chains of synthetic crystals, training on the GPU, and the seeded continuation.
+
+All arithmetic runs in libgw kernels (features, network, loss, Adam, seed, CPE); this
+module only orders the calls.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import GW, GW_CPE, GW_FP16X2, MLP
+from .driver import Chain
+
+NFIT = 64  # Matsubara points fed to the network: 2 x 64 = 128 inputs
+
+
+def chain_samples(make_crystal_grid, seeds, omega, prec=GW_FP16X2):
+    """Network inputs x [N][2 NFIT] (float32, device) from the Sigma^c(i w) of G0W0 chains,
+    one crystal per seed (make_crystal_grid(seed) -> (crystal, grid))."""
+    xs = []
+    A = None
+    for s in seeds:
+        cr, gr = make_crystal_grid(s)
+        ctx = GW(gr, cr, omega=omega)
+        ch = Chain(ctx, torch.from_numpy(cr.eps).cuda(), prec=prec, qb=4, cont_method=GW_CPE)
+        ch.start_g0()
+        ch.sigma()
+        ch.finish()
+        nprob = cr.nk * cr.nb
+        x = torch.zeros(nprob, 2 * NFIT, dtype=torch.float32, device="cuda")
+        scale = torch.zeros(nprob, dtype=torch.float64, device="cuda")
+        ctx.cpe_features(ch.Siwc, NFIT, x, scale)
+        if A is None:
+            A = torch.zeros(2 * NFIT, len(ch.cpe_x) - 2, dtype=torch.float32, device="cuda")
+            ctx.cpe_fit_matrix(NFIT, A)
+        ctx.sync()
+        xs.append(x)
+        ctx.close()
+    return torch.cat(xs), A
+
+
+def train(mlp, x, A, steps=400, batch=512, lr=1e-3, seed=0):
+    """Adam on L = (1/B) sum ||A b_hat - x||^2 over random mini-batches; returns the losses."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = x.shape[0] - x.shape[0] % batch
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    for it in range(steps):
+        idx = torch.randint(0, x.shape[0], (batch,), generator=g).cuda()
+        xb = x[idx].contiguous()
+        mlp.train_step(xb, A, lr, loss)
+        if it % 50 == 0 or it == steps - 1:
+            hist.append(float(loss.item()))
+    return hist
+
+
+def seeded_cpe(ctx, mlp, chain):
+    """Continuation of a chain's Sigma^c with the network's seed: features -> network ->
+    warm start -> gw_continue(GW_CPE). Returns the Lawson-Hanson iteration counts."""
+    nprob = chain.nk * chain.nb
+    pad = (nprob + 127) // 128 * 128
+    x = torch.zeros(pad, 2 * NFIT, dtype=torch.float32, device="cuda")
+    scale = torch.ones(nprob, dtype=torch.float64, device="cuda")
+    ctx.cpe_features(chain.Siwc, NFIT, x[:nprob], scale)
+    out = torch.zeros(pad, mlp.nout, dtype=torch.float32, device="cuda")
+    mlp.forward(x, out)
+    ctx.cpe_seed(out[:nprob].contiguous(), scale)
+    vxc = chain.Sx
+    ctx.continue_(GW_CPE, chain.Siwc, chain.eps.reshape(-1), chain.Sx.reshape(-1), vxc.reshape(-1), None, None,
+                  chain.eqp, chain.qinfo)
+    iters = torch.zeros(nprob, dtype=torch.int32, device="cuda")
+    ctx.cpe_iterations(iters)
+    return iters

@@ -365,3 +365,34 @@ def test_qp_quadratic_closed_form():
     assert ok and abs(E - want) < 1e-12
     assert abs(Z - 1 / (1 + g2 / (want - E0) ** 2)) < 1e-6
     assert orc.band_gap(np.array([[-1, 0.5], [-0.8, 0.3]]), 1) == pytest.approx(1.1)
+
+
+# ----------------------------------------------------------------------- learned CPE seed
+def test_mlp_gradient_finite_differences():
+    """Backward pass of the oracle MLP against central finite differences of its loss."""
+    from oracle import mlp
+    rng = np.random.default_rng(3)
+    sizes = [6, 8, 8, 5]
+    params = mlp.init_params(sizes, rng)
+    x = rng.standard_normal((7, 6))
+    A = rng.standard_normal((6, 5)) * 0.3
+    loss, grads = mlp.loss_and_grad(params, x, A)
+    h = 1e-6
+    for l in range(len(params)):
+        W, b = params[l]
+        for (i, j) in [(0, 0), (W.shape[0] - 1, W.shape[1] - 1), (1, 2)]:
+            Wp = W.copy(); Wp[i, j] += h
+            Wm = W.copy(); Wm[i, j] -= h
+            lp, _ = mlp.loss_and_grad(params[:l] + [(Wp, b)] + params[l + 1:], x, A)
+            lm, _ = mlp.loss_and_grad(params[:l] + [(Wm, b)] + params[l + 1:], x, A)
+            assert abs((lp - lm) / (2 * h) - grads[l][0][i, j]) < 1e-7 * (1 + abs(grads[l][0][i, j]))
+        bp = b.copy(); bp[1] += h
+        bm = b.copy(); bm[1] -= h
+        lp, _ = mlp.loss_and_grad(params[:l] + [(W, bp)] + params[l + 1:], x, A)
+        lm, _ = mlp.loss_and_grad(params[:l] + [(W, bm)] + params[l + 1:], x, A)
+        assert abs((lp - lm) / (2 * h) - grads[l][1][1]) < 1e-7 * (1 + abs(grads[l][1][1]))
+    # activations: gelu(0) = 0, gelu'(0) = 1/2, softplus >= 0, softplus' = sigmoid
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0 and abs(mlp.gelu_grad(np.array([0.0]))[0] - 0.5) < 1e-15
+    z = np.linspace(-30, 30, 13)
+    assert np.all(mlp.softplus(z) >= 0)
+    assert np.allclose((mlp.softplus(z + 1e-6) - mlp.softplus(z - 1e-6)) / 2e-6, mlp.sigmoid(z), atol=1e-8)
