@@ -171,7 +171,8 @@ def _config(cfg, args, prec):
     c = gi.CONFIGS[cfg]
     return {"workload": f"synthetic crystal {cfg}: Nk={c['nk']} (q on the same grid), Nb={c['nb']} "
                         f"({c['nocc']} occ), NI={c['ni']}, Ntau={c['ntau']}, Nnu=Nw={c['nnu']}, beta={c['beta']}",
-            "precision": prec, "omega": args.omega, "parallelism": f"q-split over {args.gpus} GPU(s)",
+            "precision": prec, "omega": args.omega, "continuation": getattr(args, "cont", "pade"),
+            "parallelism": f"q-split over {args.gpus} GPU(s)",
             "l2": "inputs larger than L2 (M tensor 69 GB, P/W per q 50 MB each)"}
 
 
@@ -182,12 +183,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="fp16x2", choices=["fp16x2", "fp64"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="nk64_nb64")
     ap.add_argument("--omega", type=float, default=None,
                     help="unit-cell volume in 1/(Omega Nk); default: the paper's Si cell, 270.1 bohr^3")
     ap.add_argument("--nq", type=int, default=0, help="limit q points (profiling / exploration only; not a bench line)")
     ap.add_argument("--nk", type=int, default=0, help="override Nk (profiling small cases only; not a bench line)")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cont", default="cpe_mlp", choices=["cpe_mlp", "cpe", "pade"],
+                    help="continuation: CPE warm-started by the learned seed (default), plain CPE, or Pade")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.omega is None:
@@ -222,9 +225,15 @@ def main():
     cnt = max(0, min(per, nq - q0))
     cr = gi.subset_q(full, q0, max(cnt, 1))
     stream = torch.cuda.current_stream()
+    cont = gw.GW_PADE if args.cont == "pade" else gw.GW_CPE
+    mlp, mlp_hist = None, None
+    if args.cont == "cpe_mlp":
+        # learned CPE seed, trained (untimed) on chains of three other crystals
+        from paper_1602_02313_gb300 import learned
+        mlp, mlp_hist = learned.trained_seed(args.omega, device=local)
     ctx = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)
     eps = torch.from_numpy(cr.eps).cuda()
-    chain = Chain(ctx, eps, prec=prec, qb=8, iqs=list(range(cnt)))
+    chain = Chain(ctx, eps, prec=prec, qb=8, iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
     fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, gr.ntau)
     flops_step = (fp + fs) * nq
 
@@ -297,9 +306,9 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            c2 = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)   # M generated from the seed
+            ctx2 = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)   # M generated from the seed
             eps_d = eps_h.to("cuda", non_blocking=True)
-            ch = Chain(c2, eps_d, prec=prec, qb=8, iqs=list(range(cnt)))
+            ch = Chain(ctx2, eps_d, prec=prec, qb=8, iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
             ch.start_g0()
             ch.sigma()
             if world > 1:
@@ -309,7 +318,7 @@ def main():
             out_h.copy_(ch.eqp, non_blocking=True)
             sx_h.copy_(ch.Sx.reshape(-1), non_blocking=True)
             torch.cuda.synchronize()
-            c2.close()
+            ctx2.close()
             del ch
         dt = (time.perf_counter() - t0) / args.e2e_steps
         if world > 1:

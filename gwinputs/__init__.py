@@ -331,13 +331,13 @@ OMEGA_SI = (5.43 / 0.529177210903) ** 3 / 4.0
 # ---------------------------------------------------------------------------
 CONFIGS = {
     # one q, Nk=8, Nb=16 (8 occ), NI=64, Ntau=16, beta=100
-    "c1": dict(seed=1001, nk=8, nb=16, nocc=8, ni=64, beta=100.0, ntau=16, nnu=16, nw=16,
+    "nk8_nb16": dict(seed=1001, nk=8, nb=16, nocc=8, ni=64, beta=100.0, ntau=16, nnu=16, nw=16,
                qlist=[1]),
     # Nk=64 (4x4x4), q on the same grid, Nb=64 (32 occ), NI=256, Ntau=48, beta=200
-    "c2": dict(seed=2001, nk=64, nb=64, nocc=32, ni=256, beta=200.0, ntau=48, nnu=48, nw=48,
+    "nk64_nb64": dict(seed=2001, nk=64, nb=64, nocc=32, ni=256, beta=200.0, ntau=48, nnu=48, nw=48,
                qlist=None),
     # Nk=216 (6x6x6), Nb=128 (48 occ), NI=512, Ntau=64, beta=400
-    "c3": dict(seed=3001, nk=216, nb=128, nocc=48, ni=512, beta=400.0, ntau=64, nnu=64, nw=64,
+    "nk216_nb128": dict(seed=3001, nk=216, nb=128, nocc=48, ni=512, beta=400.0, ntau=64, nnu=64, nw=64,
                qlist=None),
 }
 

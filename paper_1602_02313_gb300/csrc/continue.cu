@@ -3,7 +3,7 @@
 //  * CPE : continuous-pole expansion (Staar et al. 2014): Im Sigma(w + i0) piecewise linear
 //          on a real grid, Sigma(z) = sum_m b_m Phi_m(z), b_m >= 0 (causality, Im Sigma <= 0),
 //          Phi_m(z) = int hat_m(x) / (z - x) dx; b from Lawson-Hanson NNLS on the normal
-//          equations of the ridge-regularised fit (one thread block per problem).
+//          equations of the ridge-regularised fit (one warp per problem).
 //  * QP  : root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E + i eta), eta = 1e-4 Ha: the
 //          upward crossing nearest eps on a 0.005 Ha scan of eps +- 1 Ha, refined by bisection.
 #include <cuda_runtime.h>
@@ -52,25 +52,6 @@ __device__ cd cpe_phi(const double* x, int m, cd z) {
 }
 
 __device__ double resig_pade(const cd* a, int n, double beta, double E) { return pade_eval(a, n, beta, {E, kEta}).x; }
-
-// Re sum_m b_m Phi_m(E + i eta); the node logarithms are shared between neighbouring hats.
-__device__ double resig_cpe(const double* b, const double* x, int ng, double E) {
-  const cd z = {E, kEta};
-  double s = 0.0;
-  cd l0 = clog_(csub(z, cd{x[0], 0.0})), l1 = clog_(csub(z, cd{x[1], 0.0}));
-  for (int m = 0; m < ng; ++m) {
-    const cd l2 = clog_(csub(z, cd{x[m + 2], 0.0}));
-    if (b[m] != 0.0) {
-      const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
-      const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
-      const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
-      s += b[m] * (rise.x + fall.x);
-    }
-    l0 = l1;
-    l1 = l2;
-  }
-  return s;
-}
 
 // QP root nearest eps with an upward crossing of F(E) = E - eps - sx + vxc - Re Sigma^c(E):
 // scan E_j = eps + (j - 200) 0.005 Ha (j = 0..400), refine the crossing nearest eps by 60
@@ -159,176 +140,458 @@ __global__ void k_pade(int64_t nprob, const double2* __restrict__ sig, int ncont
 }
 
 // Lawson-Hanson NNLS on the normal equations N b = c (N = A^T A + lambda^2 I, c = A^T y),
-// one block per problem; N_PP is factorised by Cholesky in shared memory each solve.
+// one warp per problem. Lane l owns the grid variables m = l + 32 s and the passive-set
+// positions k = l + 32 s (s < 4). The Cholesky factor of N_PP lives in shared memory, packed
+// by rows in the order the variables joined the passive set, so that adding a variable
+// appends one row (a forward substitution, O(p^2)) and removing variables refactors only the
+// rows after the first removed one. y = L^-1 c_P is kept alongside and extended the same way.
 constexpr int kCpeMaxGrid = 128;
+constexpr int kSlots = kCpeMaxGrid / 32;
+constexpr double kSeedSupport = 1e-2;  // seed weights above this fraction of the largest start active
+constexpr int kWarmSolves = 8;         // solves allowed to turn the seed's support into a feasible point
 
-__global__ void __launch_bounds__(128) k_cpe_nnls(int64_t nprob, const double2* __restrict__ sig, int ncont,
-                                                  const double* __restrict__ A, const double* __restrict__ N, int ng,
-                                                  const double* __restrict__ b0, double* __restrict__ bout,
-                                                  int* __restrict__ info, int* __restrict__ iters) {
-  extern __shared__ double L[];  // [kCpeMaxGrid][kCpeMaxGrid], dynamic
-  __shared__ double cvec[kCpeMaxGrid], x[kCpeMaxGrid], z[kCpeMaxGrid], w[kCpeMaxGrid];
-  __shared__ int Pset[kCpeMaxGrid], idx[kCpeMaxGrid];
-  __shared__ int np_, tbest, done;
-  __shared__ double sred[128];
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_imin(int v) {
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__host__ __device__ constexpr int tri(int k) { return (k * (k + 1)) >> 1; }
+
+struct NnlsWarp {
+  double* L;     // packed lower-triangular factor, row k at tri(k)
+  double* dinv;  // 1 / L_kk
+  double* cv;    // c = A^T y by variable
+  double* xv;    // current iterate by variable
+  double* zv;    // passive-set least-squares solution by variable (0 off the set)
+  int* idx;      // passive variables in the order they joined
+  int* pf;       // passive flag by variable
+  int* lst;      // scratch list of variables
+};
+
+// Appends variable m as row p: l = L^-1 N_{P,m} (column-oriented forward substitution over
+// lane-owned partial sums), pivot sqrt(N_mm - l.l) and the new entry of y. Returns false
+// (warp-uniform) when the pivot is not positive.
+__device__ bool chol_append(const NnlsWarp& S, const double* __restrict__ N, int ng, int p, int m,
+                            double (&yv)[kSlots], int lane) {
+  double r[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = lane + 32 * s;
+    r[s] = k < p ? N[(size_t)m * ng + S.idx[k]] : 0.0;
+  }
+#pragma unroll
+  for (int sk = 0; sk < kSlots; ++sk) {
+    if (32 * sk >= p) break;
+    const int kend = min(32, p - 32 * sk);
+    for (int kk = 0; kk < kend; ++kk) {
+      const int k = 32 * sk + kk;
+      const double lk = __shfl_sync(0xffffffffu, r[sk], kk) * S.dinv[k];
+#pragma unroll
+      for (int s = sk; s < kSlots; ++s) {
+        const int i = lane + 32 * s;
+        if (i > k && i < p) r[s] = fma(-S.L[tri(i) + k], lk, r[s]);
+      }
+    }
+  }
+  double ll = 0.0, ly = 0.0;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = lane + 32 * s;
+    if (k < p) {
+      const double l = r[s] * S.dinv[k];
+      S.L[tri(p) + k] = l;
+      ll = fma(l, l, ll);
+      ly = fma(l, yv[s], ly);
+    }
+  }
+  ll = warp_sum(ll);
+  ly = warp_sum(ly);
+  const double d = N[(size_t)m * ng + m] - ll;
+  if (!(d > 0.0)) return false;
+  const double piv = sqrt(d);
+  const double ynew = (S.cv[m] - ly) / piv;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s)
+    if (lane + 32 * s == p) yv[s] = ynew;
+  if (lane == 0) {
+    S.L[tri(p) + p] = piv;
+    S.dinv[p] = 1.0 / piv;
+    S.idx[p] = m;
+    S.pf[m] = 1;
+  }
+  __syncwarp();
+  return true;
+}
+
+// z_P = L^-T y (column-oriented backward substitution), scattered into zv by variable.
+__device__ void chol_solve(const NnlsWarp& S, int p, const double (&yv)[kSlots], int lane) {
+  double t[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) t[s] = yv[s];
+#pragma unroll
+  for (int sk = kSlots - 1; sk >= 0; --sk) {
+    if (32 * sk >= p) continue;
+    const int kend = min(32, p - 32 * sk);
+    for (int kk = kend - 1; kk >= 0; --kk) {
+      const int k = 32 * sk + kk;
+      const double zk = __shfl_sync(0xffffffffu, t[sk], kk) * S.dinv[k];
+#pragma unroll
+      for (int s = 0; s <= sk; ++s) {
+        const int j = lane + 32 * s;
+        if (j < k) t[s] = fma(-S.L[tri(k) + j], zk, t[s]);
+      }
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) S.zv[lane + 32 * s] = 0.0;
+  __syncwarp();
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = lane + 32 * s;
+    if (k < p) S.zv[S.idx[k]] = t[s] * S.dinv[k];
+  }
+  __syncwarp();
+}
+
+// After variables left the passive set (pf cleared): compacts the position list, keeps the
+// factor rows before the first removed position and re-appends the rest. Returns the new
+// size, or -1 if a pivot failed.
+__device__ int chol_remove(const NnlsWarp& S, const double* __restrict__ N, int ng, int p, double (&yv)[kSlots],
+                           int lane) {
+  int kf = p;
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int k = lane + 32 * s;
+    if (k < p && !S.pf[S.idx[k]]) kf = min(kf, k);
+  }
+  kf = warp_imin(kf);
+  if (kf == p) return p;
+  int base = kf;
+  for (int k0 = kf; k0 < p; k0 += 32) {
+    const int k = k0 + lane;
+    const int m = k < p ? S.idx[k] : -1;
+    const bool keep = k < p && S.pf[m];
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();
+    if (keep) S.idx[base + __popc(bal & ((1u << lane) - 1u))] = m;
+    base += __popc(bal);
+    __syncwarp();
+  }
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s)
+    if (lane + 32 * s >= kf) yv[s] = 0.0;
+  for (int k = kf; k < base; ++k)
+    if (!chol_append(S, N, ng, k, S.idx[k], yv, lane)) return -1;
+  return base;
+}
+
+__global__ void __launch_bounds__(32) k_cpe_nnls(int64_t nprob, const double2* __restrict__ sig, int ncont,
+                                                 const double* __restrict__ A, const double* __restrict__ N, int ng,
+                                                 const double* __restrict__ b0, double* __restrict__ bout,
+                                                 int* __restrict__ info, int* __restrict__ iters) {
+  extern __shared__ double sm[];
+  NnlsWarp S;
+  S.L = sm;
+  S.dinv = S.L + tri(ng);
+  S.cv = S.dinv + kCpeMaxGrid;
+  S.xv = S.cv + kCpeMaxGrid;
+  S.zv = S.xv + kCpeMaxGrid;
+  S.idx = reinterpret_cast<int*>(S.zv + kCpeMaxGrid);
+  S.pf = S.idx + kCpeMaxGrid;
+  S.lst = S.pf + kCpeMaxGrid;
   const int64_t prob = blockIdx.x;
-  const int t = threadIdx.x;
-  const double2* y = sig + (size_t)prob * ncont;
+  const int lane = threadIdx.x;
+  const double2* yin = sig + (size_t)prob * ncont;
   // c = A^T y, A = [Re Phi ; Im Phi] (2 ncont x ng)
-  for (int m = t; m < ng; m += blockDim.x) {
-    double s = 0.0;
-    for (int n = 0; n < ncont; ++n) {
-      s = fma(A[(size_t)n * ng + m], y[n].x, s);
-      s = fma(A[(size_t)(ncont + n) * ng + m], y[n].y, s);
-    }
-    cvec[m] = s;
-    x[m] = 0.0;
-    Pset[m] = 0;
-  }
-  __syncthreads();
-  if (b0) {
-    // warm start: passive set = support of the seed, then one feasible LS solve below
-    for (int m = t; m < ng; m += blockDim.x) {
-      const double v = b0[(size_t)prob * ng + m];
-      Pset[m] = v > 0.0 ? 1 : 0;
-      x[m] = v > 0.0 ? v : 0.0;
-    }
-  }
-  __syncthreads();
   double cmax = 0.0;
-  for (int m = 0; m < ng; ++m) cmax = fmax(cmax, fabs(cvec[m]));
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) {
+    const int m = lane + 32 * s;
+    double c = 0.0;
+    if (m < ng)
+      for (int n = 0; n < ncont; ++n) {
+        c = fma(A[(size_t)n * ng + m], yin[n].x, c);
+        c = fma(A[(size_t)(ncont + n) * ng + m], yin[n].y, c);
+      }
+    S.cv[m] = c;
+    S.xv[m] = 0.0;
+    S.zv[m] = 0.0;
+    S.pf[m] = 0;
+    cmax = fmax(cmax, fabs(c));
+  }
+  for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+  __syncwarp();
   const double tol = 1e-13 * fmax(cmax, 1e-300);
-  int outer = 0, status = 0;
-  bool need_solve = b0 != nullptr;
+  double yv[kSlots];
+#pragma unroll
+  for (int s = 0; s < kSlots; ++s) yv[s] = 0.0;
+  int p = 0, outer = 0, status = 0, warm = -1;
+  bool need_solve = false;
+  if (b0) {
+    // warm start: the passive set is the support of the seed (weights above kSeedSupport of
+    // the largest), factorised by appends in increasing variable order
+    double mx = 0.0;
+    for (int m = lane; m < ng; m += 32) mx = fmax(mx, b0[(size_t)prob * ng + m]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int nsel = 0;
+    for (int m0 = 0; m0 < ng; m0 += 32) {
+      const int m = m0 + lane;
+      const bool on = m < ng && mx > 0.0 && b0[(size_t)prob * ng + m] > kSeedSupport * mx;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (on) S.lst[nsel + __popc(bal & ((1u << lane) - 1u))] = m;
+      nsel += __popc(bal);
+    }
+    __syncwarp();
+    for (int q = 0; q < nsel; ++q)
+      if (chol_append(S, N, ng, p, S.lst[q], yv, lane)) ++p;
+    if (p > 0) {
+      need_solve = true;
+      warm = kWarmSolves;
+    }
+  }
   while (true) {
     if (!need_solve) {
-      // gradient w = c - N x; pick the most violating inactive index
-      for (int m = t; m < ng; m += blockDim.x) {
-        double s = cvec[m];
-        for (int j = 0; j < ng; ++j)
-          if (x[j] != 0.0) s -= N[(size_t)m * ng + j] * x[j];
-        w[m] = s;
+      // gradient w = c - N x on the inactive variables; the largest positive one joins
+      double w[kSlots];
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) w[s] = S.cv[lane + 32 * s];
+      for (int k = 0; k < p; ++k) {
+        const int mk = S.idx[k];
+        const double xk = S.xv[mk];
+        const double* Nr = N + (size_t)mk * ng;
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          const int m = lane + 32 * s;
+          if (m < ng) w[s] = fma(-Nr[m], xk, w[s]);
+        }
       }
-      __syncthreads();
-      if (t == 0) {
-        int best = -1;
-        double bw = tol;
-        for (int m = 0; m < ng; ++m)
-          if (!Pset[m] && w[m] > bw) {
-            bw = w[m];
-            best = m;
-          }
-        tbest = best;
-        if (best >= 0) Pset[best] = 1;
+      double bw = tol;
+      int best = -1;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        const int m = lane + 32 * s;
+        if (m < ng && !S.pf[m] && w[s] > bw) {
+          bw = w[s];
+          best = m;
+        }
       }
-      __syncthreads();
-      if (tbest < 0) break;
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, bw, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, best, o);
+        if (ob > bw || (ob == bw && oi >= 0 && (best < 0 || oi < best))) {
+          bw = ob;
+          best = oi;
+        }
+      }
+      if (best < 0) break;
       if (++outer > 3 * ng) {
         status = 2;
         break;
       }
+      if (!chol_append(S, N, ng, p, best, yv, lane)) {
+        status = 3;
+        break;
+      }
+      ++p;
     }
     need_solve = false;
+    bool done = false;
     // inner loop: solve on the passive set, step back to feasibility if needed
     for (int inner = 0; inner < 3 * ng; ++inner) {
-      if (t == 0) {
-        int c = 0;
-        for (int m = 0; m < ng; ++m)
-          if (Pset[m]) idx[c++] = m;
-        np_ = c;
+      chol_solve(S, p, yv, lane);
+      // alpha = min over passive z <= 0 of x / (x - z)
+      double alpha = 2.0;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        const int m = lane + 32 * s;
+        if (m < ng && S.pf[m] && S.zv[m] <= 0.0) alpha = fmin(alpha, S.xv[m] / (S.xv[m] - S.zv[m]));
       }
-      __syncthreads();
-      const int p = np_;
-      for (int e = t; e < p * p; e += blockDim.x) {
-        const int r = e / p, s = e % p;
-        L[r * kCpeMaxGrid + s] = N[(size_t)idx[r] * ng + idx[s]];
+      alpha = warp_min(alpha);
+      if (alpha > 1.0) {
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) S.xv[lane + 32 * s] = S.zv[lane + 32 * s];
+        __syncwarp();
+        done = true;
+        break;
       }
-      __syncthreads();
-      // Cholesky N_PP = L L^T (lower triangle, in place)
-      for (int j = 0; j < p; ++j) {
-        if (t == 0) {
-          double d = L[j * kCpeMaxGrid + j];
-          for (int k = 0; k < j; ++k) d -= L[j * kCpeMaxGrid + k] * L[j * kCpeMaxGrid + k];
-          L[j * kCpeMaxGrid + j] = sqrt(fmax(d, 1e-300));
-        }
-        __syncthreads();
-        for (int i = j + 1 + t; i < p; i += blockDim.x) {
-          double s = L[i * kCpeMaxGrid + j];
-          for (int k = 0; k < j; ++k) s -= L[i * kCpeMaxGrid + k] * L[j * kCpeMaxGrid + k];
-          L[i * kCpeMaxGrid + j] = s / L[j * kCpeMaxGrid + j];
-        }
-        __syncthreads();
-      }
-      if (t == 0) {
-        // forward / backward substitution into z (compressed), then scatter
-        for (int i = 0; i < p; ++i) {
-          double s = cvec[idx[i]];
-          for (int k = 0; k < i; ++k) s -= L[i * kCpeMaxGrid + k] * sred[k];
-          sred[i] = s / L[i * kCpeMaxGrid + i];
-        }
-        for (int i = p - 1; i >= 0; --i) {
-          double s = sred[i];
-          for (int k = i + 1; k < p; ++k) s -= L[k * kCpeMaxGrid + i] * sred[k];
-          sred[i] = s / L[i * kCpeMaxGrid + i];
-        }
-        for (int m = 0; m < ng; ++m) z[m] = 0.0;
-        for (int i = 0; i < p; ++i) z[idx[i]] = sred[i];
-        // feasibility
-        double alpha = 2.0;
-        for (int i = 0; i < p; ++i) {
-          const int m = idx[i];
-          if (z[m] <= 0.0) {
-            const double a = x[m] / (x[m] - z[m]);
-            if (a < alpha) alpha = a;
-          }
-        }
-        if (alpha > 1.0) {
-          for (int m = 0; m < ng; ++m) x[m] = z[m];
-          done = 1;
+#pragma unroll
+      for (int s = 0; s < kSlots; ++s) {
+        const int m = lane + 32 * s;
+        if (warm > 0) {
+          // warm start: the seed's support need not be feasible; instead of stepping back
+          // one variable at a time, every non-positive variable of the solve leaves and the
+          // rest is solved again (at most kWarmSolves times, else a cold restart from x = 0)
+          if (S.pf[m] && S.zv[m] <= 0.0) S.pf[m] = 0;
+          S.xv[m] = 0.0;
         } else {
-          for (int m = 0; m < ng; ++m) {
-            x[m] += alpha * (z[m] - x[m]);
-            if (Pset[m] && x[m] <= 1e-300) {
-              x[m] = 0.0;
-              Pset[m] = 0;
-            }
+          double xm = S.xv[m] + alpha * (S.zv[m] - S.xv[m]);
+          if (S.pf[m] && xm <= 1e-300) {
+            xm = 0.0;
+            S.pf[m] = 0;
           }
-          done = 0;
+          S.xv[m] = xm;
         }
       }
-      __syncthreads();
-      if (done) break;
+      __syncwarp();
+      p = chol_remove(S, N, ng, p, yv, lane);
+      if (p < 0) {
+        status = 3;
+        break;
+      }
+      if (warm > 0 && --warm == 0) break;
+    }
+    if (status == 3) break;
+    if (warm >= 0) {
+      if (!done) {
+        // cold restart
+#pragma unroll
+        for (int s = 0; s < kSlots; ++s) {
+          S.xv[lane + 32 * s] = 0.0;
+          S.pf[lane + 32 * s] = 0;
+          yv[s] = 0.0;
+        }
+        p = 0;
+        __syncwarp();
+      }
+      warm = -1;
     }
   }
-  for (int m = t; m < ng; m += blockDim.x) bout[(size_t)prob * ng + m] = x[m];
-  if (t == 0) {
+  for (int m = lane; m < ng; m += 32) bout[(size_t)prob * ng + m] = S.xv[m];
+  if (lane == 0) {
     info[prob] = status;
     if (iters) iters[prob] = outer;
   }
+}
+
+__host__ __device__ constexpr size_t nnls_smem_bytes(int ng) {
+  return sizeof(double) * ((size_t)tri(ng) + 4 * kCpeMaxGrid) + sizeof(int) * 3 * kCpeMaxGrid;
+}
+
+// Real-axis values and QP root, one warp per problem: the 401 scan points are split over
+// the lanes (each lane sums all hats at its own energies); the bisection evaluates one
+// energy per step with the hats split over the lanes and a warp sum.
+// Re sum_m b_m Phi_m(E + i eta) by one thread; the node logarithms are shared between neighbouring hats.
+__device__ double resig_cpe_lane(const double* b, const double* x, int ng, double E) {
+  const cd z = {E, kEta};
+  double s = 0.0;
+  cd l0 = clog_(csub(z, cd{x[0], 0.0})), l1 = clog_(csub(z, cd{x[1], 0.0}));
+  for (int m = 0; m < ng; ++m) {
+    const cd l2 = clog_(csub(z, cd{x[m + 2], 0.0}));
+    if (b[m] != 0.0) {
+      const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
+      const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
+      const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
+      s += b[m] * (rise.x + fall.x);
+    }
+    l0 = l1;
+    l1 = l2;
+  }
+  return s;
+}
+__device__ double resig_cpe_warp(const double* b, const double* x, int ng, double E, int lane) {
+  const cd z = {E, kEta};
+  double s = 0.0;
+  for (int m = lane; m < ng; m += 32) {
+    if (b[m] == 0.0) continue;
+    const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
+    const cd l0 = clog_(csub(z, cd{x0, 0.0})), l1 = clog_(csub(z, cd{x1, 0.0})), l2 = clog_(csub(z, cd{x2, 0.0}));
+    const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
+    const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
+    s += b[m] * (rise.x + fall.x);
+  }
+  return warp_sum(s);
 }
 
 __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const double* __restrict__ x, int ng,
                          const double* __restrict__ eps, const double* __restrict__ sigx,
                          const double* __restrict__ vxc, int nreal, const double* __restrict__ wr,
                          double2* __restrict__ sreal, double* __restrict__ eqp, int* __restrict__ info) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (p >= nprob) return;
   const double* bp = b + (size_t)p * ng;
   for (int r = 0; r < nreal; ++r) {
-    cd s = {0.0, 0.0};
-    for (int m = 0; m < ng; ++m)
+    double sx_ = 0.0, sy_ = 0.0;
+    for (int m = lane; m < ng; m += 32)
       if (bp[m] != 0.0) {
         const cd ph = cpe_phi(x, m, {wr[r], kEta});
-        s.x += bp[m] * ph.x;
-        s.y += bp[m] * ph.y;
+        sx_ += bp[m] * ph.x;
+        sy_ += bp[m] * ph.y;
       }
-    sreal[(size_t)p * nreal + r] = make_double2(s.x, s.y);
+    sx_ = warp_sum(sx_);
+    sy_ = warp_sum(sy_);
+    if (lane == 0) sreal[(size_t)p * nreal + r] = make_double2(sx_, sy_);
+  }
+  const double e0 = eps[p], s0 = sigx[p], v0 = vxc[p];
+  auto F = [&](double E) { return E - e0 - s0 + v0 - resig_cpe_warp(bp, x, ng, E, lane); };
+  // scan: F at E_j = e0 + (j - 200) kQpStep, j = 0 .. 400; lanes take consecutive blocks
+  constexpr int per = (kQpScan + 31) / 32;  // 13 points per lane
+  double fv[per + 1];
+  for (int q = 0; q <= per; ++q) {
+    const int j = lane * per + q;
+    const int jj = j < kQpScan ? j : kQpScan - 1;
+    const double E = e0 + (jj - kQpScan / 2) * kQpStep;
+    fv[q] = E - e0 - s0 + v0 - resig_cpe_lane(bp, x, ng, E);
+  }
+  int best = -1;
+  double bestd = 0.0;
+  for (int q = 0; q < per; ++q) {
+    const int j = lane * per + q;
+    if (j + 1 >= kQpScan) break;
+    if (fv[q] < 0.0 && fv[q + 1] >= 0.0) {
+      const double d = fabs(0.5 * ((e0 + (j - kQpScan / 2) * kQpStep) + (e0 + (j + 1 - kQpScan / 2) * kQpStep)) - e0);
+      if (best < 0 || d < bestd || (d == bestd && j < best)) {
+        best = j;
+        bestd = d;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const int ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const double od = __shfl_xor_sync(0xffffffffu, bestd, o);
+    if (ob >= 0 && (best < 0 || od < bestd || (od == bestd && ob < best))) {
+      best = ob;
+      bestd = od;
+    }
   }
   double E;
   int ok;
-  qp_solve([&](double e) { return resig_cpe(bp, x, ng, e); }, eps[p], sigx[p], vxc[p], &E, &ok);
-  eqp[p] = E;
-  if (info[p] == 0 && !ok) info[p] = 1;
+  if (best >= 0) {
+    double lo = e0 + (best - kQpScan / 2) * kQpStep, hi = e0 + (best + 1 - kQpScan / 2) * kQpStep;
+    for (int it = 0; it < 60; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (F(mid) < 0.0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    E = 0.5 * (lo + hi);
+    ok = 1;
+  } else {
+    E = e0;
+    ok = 0;
+    const double de = 1e-6;
+    for (int it = 0; it < 100; ++it) {
+      const double Fv = F(E);
+      const double dF = 1.0 - (resig_cpe_warp(bp, x, ng, E + de, lane) - resig_cpe_warp(bp, x, ng, E - de, lane)) /
+                                  (2.0 * de);
+      if (dF == 0.0 || !isfinite(dF)) break;
+      double step = fmax(-0.5, fmin(0.5, Fv / dF));
+      E -= step;
+      if (fabs(step) < 1e-12 * fmax(1.0, fabs(E))) break;
+    }
+  }
+  if (lane == 0) {
+    eqp[p] = E;
+    if (info[p] == 0 && !ok) info[p] = 1;
+  }
 }
 
 }  // namespace
@@ -354,7 +617,7 @@ gw_status launch_continue(gw_ctx* c, int method, int64_t nprob, const double* si
     }
     c->cpe_b_bytes = need;
   }
-  const size_t smem = sizeof(double) * kCpeMaxGrid * kCpeMaxGrid;
+  const size_t smem = nnls_smem_bytes(c->cpe_ngrid);
   cudaFuncSetAttribute(k_cpe_nnls, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   c->cpe_nprob = nprob;
   if ((size_t)nprob * sizeof(int) > c->cpe_iters_bytes) {
@@ -370,11 +633,11 @@ gw_status launch_continue(gw_ctx* c, int method, int64_t nprob, const double* si
   const double* seed = nullptr;
   if (c->cpe_seed_nprob == nprob) seed = c->d_cpe_seed;  // a seed set by gw_cpe_seed, consumed once
   c->cpe_seed_nprob = 0;
-  k_cpe_nnls<<<(unsigned)nprob, 128, smem, c->stream>>>(nprob, (const double2*)sig_iw, c->ncont, c->d_cpe_A, c->d_cpe_N,
+  k_cpe_nnls<<<(unsigned)nprob, 32, smem, c->stream>>>(nprob, (const double2*)sig_iw, c->ncont, c->d_cpe_A, c->d_cpe_N,
                                                      c->cpe_ngrid, seed, c->d_cpe_b, info, c->d_cpe_iters);
   gw_status s = check_launch(c, "cpe_nnls");
   if (s != GW_OK) return s;
-  k_cpe_qp<<<(unsigned)((nprob + 63) / 64), 64, 0, c->stream>>>(nprob, c->d_cpe_b, c->d_cpe_x, c->cpe_ngrid, eps,
+  k_cpe_qp<<<(unsigned)((nprob + 3) / 4), 128, 0, c->stream>>>(nprob, c->d_cpe_b, c->d_cpe_x, c->cpe_ngrid, eps,
                                                                  sigx, vxc, nreal, omega_real, (double2*)sig_real,
                                                                  e_qp, info);
   return check_launch(c, "cpe_qp");

@@ -38,7 +38,8 @@ def contraction_flops(nk, nb, ni, ntau):
 class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
-    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-5):
+    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-5, mlp=None,
+                 nfit=64):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
@@ -68,9 +69,18 @@ class Chain:
         self.qinfo = torch.zeros(nk * nb, dtype=torch.int32, **d)
         self.vxc = None
         self.timers = None
+        self.mlp = mlp
         if cont_method == GW_CPE:
             self.cpe_x = cpe_grid()
             ctx.cpe_setup(self.cpe_x, cpe_ridge)
+        if mlp is not None:
+            # learned seed of the CPE fit: network input / output buffers (rows padded to 128)
+            nprob = nk * nb
+            pad = (nprob + 127) // 128 * 128
+            self.nfit = nfit
+            self.feat = torch.zeros(pad, 2 * nfit, dtype=torch.float32, **d)
+            self.scale = torch.ones(nprob, dtype=f8, **d)
+            self.bhat = torch.zeros(pad, mlp.nout, dtype=torch.float32, **d)
 
     def _timed(self, key, fn):
         if self.timers is None:
@@ -114,6 +124,11 @@ class Chain:
         ctx.tau_to_freq(GW_FERMI, GW_TAU_TO_IW, nkb, self.S, self.Siw)
         ctx.tau_to_freq(GW_FERMI, GW_TAU_TO_IW_CONT, nkb, self.S, self.Siwc)
         ctx.green_tau(self.eps, self.G1, self.occ1, self.Sx, vxc, self.Siw)
+        if self.mlp is not None and self.cont_method == GW_CPE:
+            nprob = nkb
+            ctx.cpe_features(self.Siwc, self.nfit, self.feat[:nprob], self.scale)
+            self.mlp.forward(self.feat, self.bhat)
+            ctx.cpe_seed(self.bhat[:nprob], self.scale)
         ctx.continue_(self.cont_method, self.Siwc, self.eps.reshape(-1), self.Sx.reshape(-1),
                       vxc.reshape(-1), None, None, self.eqp, self.qinfo)
 

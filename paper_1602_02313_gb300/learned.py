@@ -64,10 +64,20 @@ def seeded_cpe(ctx, mlp, chain):
     ctx.cpe_features(chain.Siwc, NFIT, x[:nprob], scale)
     out = torch.zeros(pad, mlp.nout, dtype=torch.float32, device="cuda")
     mlp.forward(x, out)
-    ctx.cpe_seed(out[:nprob].contiguous(), scale)
+    ctx.cpe_seed(out[:nprob], scale)
     vxc = chain.Sx
     ctx.continue_(GW_CPE, chain.Siwc, chain.eps.reshape(-1), chain.Sx.reshape(-1), vxc.reshape(-1), None, None,
                   chain.eqp, chain.qinfo)
     iters = torch.zeros(nprob, dtype=torch.int32, device="cuda")
     ctx.cpe_iterations(iters)
     return iters
+
+
+def trained_seed(omega, seeds=(9001, 9002, 9003), steps=400, device=0):
+    """A network trained on the G0W0 chains of crystals with the Nk=64 crystal's band and basis sizes (Nk = 8) and the given
+    seeds (kept apart from the benchmarked crystal's seed)."""
+    import gwinputs as gi
+    x, A = chain_samples(lambda s: gi.make_config("nk64_nb64", nk=8, seed=s), list(seeds), omega)
+    net = MLP(seed=17, device=device)
+    hist = train(net, x, A, steps=steps, batch=512, lr=1e-3)
+    return net, hist

@@ -58,7 +58,7 @@ def test_training_and_seed_gain(gw):
 
     from paper_1602_02313_gb300 import learned
     from paper_1602_02313_gb300.driver import Chain
-    mk = lambda s: gi.make_config("c2", nk=8, seed=s)  # noqa: E731
+    mk = lambda s: gi.make_config("nk64_nb64", nk=8, seed=s)  # noqa: E731
     x, A = learned.chain_samples(mk, [5001, 5002, 5003], gi.OMEGA_SI)
     net = gw.MLP(seed=11)
     hist = learned.train(net, x, A, steps=400, batch=512, lr=1e-3)

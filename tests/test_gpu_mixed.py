@@ -48,7 +48,7 @@ def rel(a, b):
 
 
 def cases():
-    yield "c1", gi.make_config("c1")
+    yield "nk8_nb16", gi.make_config("nk8_nb16")
     yield "ragged", (gi.make_crystal(77, 3, 5, 2, 32, 30.0, qlist=[1, 2]), gi.make_grid(30.0, 8, 8, 8, ncont=24))
     yield "ni160", (gi.make_crystal(78, 8, 12, 5, 160, 50.0, qlist=[3]), gi.make_grid(50.0, 12, 12, 12, ncont=24))
 
@@ -93,7 +93,7 @@ def test_selfenergy_tc(gw, name, case):
 def test_c2_full_size_tc_vs_fp64(gw):
     """Bench sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): tensor-core P and Sigma of
     one q against the FP64 GPU path (itself pinned to the oracle in test_gpu_parity)."""
-    cr, gr = gi.make_config("c2", qlist=[7])
+    cr, gr = gi.make_config("nk64_nb64", qlist=[7])
     ctx = gw.GW(gr, cr)
     G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
     Gd = dev(G)
@@ -103,7 +103,7 @@ def test_c2_full_size_tc_vs_fp64(gw):
     ctx.polarization(0, Gd, P16, gw.GW_FP16X2)
     ctx.sync()
     e = rel(host(P16), host(P64))
-    print(f"c2: P tensor-core vs FP64 rel err {e:.3e}")
+    print(f"Nk=64: P tensor-core vs FP64 rel err {e:.3e}")
     assert e < TOL_P
     rng = np.random.default_rng(4)
     X = rng.standard_normal((gr.ntau, cr.ni, 16)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 16))
@@ -114,16 +114,16 @@ def test_c2_full_size_tc_vs_fp64(gw):
     ctx.selfenergy(0, Gd, dev(occ), W, S16, None, gw.GW_FP16X2)
     ctx.sync()
     e = rel(host(S16), host(S64))
-    print(f"c2: Sigma tensor-core vs FP64 rel err {e:.3e}")
+    print(f"Nk=64: Sigma tensor-core vs FP64 rel err {e:.3e}")
     assert e < TOL_S
 
 
 def test_chain_qp_gap_mixed_vs_fp64(gw):
-    """Whole G0W0 chain (all q) with c2 shapes at Nk = 8 and the paper's silicon cell volume:
+    """Whole G0W0 chain (all q) with the Nk=64 crystal's shapes at Nk = 8 and the paper's silicon cell volume:
     quasiparticle energies and the band gap from the tensor-core path against the FP64 path,
     with Pade and with CPE continuation. Reported with the |Sigma| scale it was measured at."""
     from paper_1602_02313_gb300.driver import Chain
-    cr, gr = gi.make_config("c2", nk=8)
+    cr, gr = gi.make_config("nk64_nb64", nk=8)
     res = {}
     for name, prec in [("fp64", gw.GW_FP64), ("fp16x2", gw.GW_FP16X2)]:
         for cont in (gw.GW_PADE, gw.GW_CPE):

@@ -42,7 +42,7 @@ def rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-def small_case(name="c1", **over):
+def small_case(name="nk8_nb16", **over):
     cr, gr = gi.make_config(name, **over)
     return cr, gr
 
@@ -55,15 +55,15 @@ def ragged_case():
 
 
 @pytest.fixture(scope="module")
-def c1(gw):
+def small(gw):
     cr, gr = small_case()
     ctx = gw.GW(gr, cr, omega=1.0)
     return cr, gr, ctx
 
 
 # ------------------------------------------------------------------ inputs
-def test_matrix_elements_match_generator(gw, c1):
-    cr, gr, ctx = c1
+def test_matrix_elements_match_generator(gw, small):
+    cr, gr, ctx = small
     out = zeros((cr.nk, cr.ni, cr.nb, cr.nb), "c16")
     ctx.copy_m(0, 0, cr.nk, out)
     ctx.sync()
@@ -72,8 +72,8 @@ def test_matrix_elements_match_generator(gw, c1):
 
 
 # ------------------------------------------------------------------ G
-def test_green0(gw, c1):
-    cr, gr, ctx = c1
+def test_green0(gw, small):
+    cr, gr, ctx = small
     G = zeros((cr.nk, cr.nb, gr.ntau))
     occ = zeros((cr.nk, cr.nb))
     ctx.green_tau(dev(cr.eps), G, occ)
@@ -84,9 +84,9 @@ def test_green0(gw, c1):
 
 
 # ------------------------------------------------------------------ P
-@pytest.mark.parametrize("case", ["c1", "ragged"])
+@pytest.mark.parametrize("case", ["nk8_nb16", "ragged"])
 def test_polarization_fp64(gw, case):
-    cr, gr = small_case() if case == "c1" else ragged_case()
+    cr, gr = small_case() if case == "nk8_nb16" else ragged_case()
     ctx = gw.GW(gr, cr, omega=1.3)
     G, _ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
     for iq in range(cr.nq):
@@ -98,9 +98,9 @@ def test_polarization_fp64(gw, case):
 
 
 # ------------------------------------------------------------------ transforms
-@pytest.mark.parametrize("case", ["c1", "ragged"])
+@pytest.mark.parametrize("case", ["nk8_nb16", "ragged"])
 def test_transforms(gw, case):
-    cr, gr = small_case() if case == "c1" else ragged_case()
+    cr, gr = small_case() if case == "nk8_nb16" else ragged_case()
     ctx = gw.GW(gr, cr)
     T = orc.transform_matrices(gr)
     rng = np.random.default_rng(3)
@@ -129,9 +129,9 @@ def test_transforms(gw, case):
 
 
 # ------------------------------------------------------------------ screen
-@pytest.mark.parametrize("case", ["c1", "ragged"])
+@pytest.mark.parametrize("case", ["nk8_nb16", "ragged"])
 def test_screen(gw, case):
-    cr, gr = small_case() if case == "c1" else ragged_case()
+    cr, gr = small_case() if case == "nk8_nb16" else ragged_case()
     ctx = gw.GW(gr, cr, omega=0.7)
     P = np.stack([orc.lindhard_iv(gi.m_for_q(cr, iq), cr.eps, cr.kmq[iq], gr.nu_idx, gr.beta, omega=0.7)
                   for iq in range(cr.nq)])
@@ -145,9 +145,9 @@ def test_screen(gw, case):
 
 
 # ------------------------------------------------------------------ self-energy
-@pytest.mark.parametrize("case", ["c1", "ragged"])
+@pytest.mark.parametrize("case", ["nk8_nb16", "ragged"])
 def test_selfenergy_fp64(gw, case):
-    cr, gr = small_case() if case == "c1" else ragged_case()
+    cr, gr = small_case() if case == "nk8_nb16" else ragged_case()
     ctx = gw.GW(gr, cr, omega=1.1)
     G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
     rng = np.random.default_rng(5)
@@ -169,8 +169,8 @@ def test_selfenergy_fp64(gw, case):
 
 
 # ------------------------------------------------------------------ Dyson
-def test_dyson(gw, c1):
-    cr, gr, ctx = c1
+def test_dyson(gw, small):
+    cr, gr, ctx = small
     rng = np.random.default_rng(8)
     sx = rng.uniform(-3, -1, (cr.nk, cr.nb))
     vxc = sx + rng.uniform(-0.01, 0.01, (cr.nk, cr.nb))
@@ -194,8 +194,8 @@ def _model_sigma(nprob, ncont, beta, seed=0):
     return (r[:, None, :] / (z[None, :, None] - e[:, None, :])).sum(-1), e, r
 
 
-def test_pade_and_qp(gw, c1):
-    cr, gr, ctx = c1
+def test_pade_and_qp(gw, small):
+    cr, gr, ctx = small
     nprob = 20
     sig, _, _ = _model_sigma(nprob, gr.ncont, gr.beta)
     eps = np.linspace(-0.9, 0.9, nprob)
@@ -218,8 +218,8 @@ def test_pade_and_qp(gw, c1):
         assert (host(info)[p] == 0) == ok
 
 
-def test_cpe_and_qp(gw, c1):
-    cr, gr, ctx = c1
+def test_cpe_and_qp(gw, small):
+    cr, gr, ctx = small
     nprob = 12
     sig, _, _ = _model_sigma(nprob, gr.ncont, gr.beta, seed=1)
     x = orc.cpe_grid(64, 0.02, 20.0)
@@ -250,11 +250,11 @@ def test_cpe_and_qp(gw, c1):
         assert abs(host(eq)[p] - E) < 1e-9
 
 
-# ------------------------------------------------------------------ whole chain (c1)
-def test_g0w0_chain_c1(gw, c1):
+# ------------------------------------------------------------------ whole chain (Nk=8, one q)
+def test_g0w0_chain_small(gw, small):
     """G0 -> P -> P(i nu) -> W~(i nu) -> W~(tau) -> Sigma(tau) -> Sigma(i w) -> Dyson G,
     every step on the GPU, against the same chain in the oracle."""
-    cr, gr, ctx = c1
+    cr, gr, ctx = small
     import torch
     G = zeros((cr.nk, cr.nb, gr.ntau))
     occ = zeros((cr.nk, cr.nb))
@@ -297,11 +297,11 @@ def test_g0w0_chain_c1(gw, c1):
     assert np.abs(host(occ1) - occ1r).max() < TOL
 
 
-# ------------------------------------------------------------------ full size (c2), sampled
+# ------------------------------------------------------------------ full size (Nk=64, Nb=64, NI=256), sampled
 def test_c2_full_size_sampled(gw):
     """The bench workload's sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): FP64 P of
     one q at sampled tau, and Sigma^c at sampled (k, tau), against the oracle."""
-    cr, gr = gi.make_config("c2", qlist=[5])
+    cr, gr = gi.make_config("nk64_nb64", qlist=[5])
     ctx = gw.GW(gr, cr)
     G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
     P = zeros((gr.ntau, cr.ni, cr.ni), "c16")

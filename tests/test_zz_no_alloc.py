@@ -25,7 +25,7 @@ def test_screen_static_matches_screen():
     from paper_1602_02313_gb300 import build as b
     b.build()
     lib = gw.load_library()
-    # c2-sized systems (NI = 256, 48 bosonic frequencies): 96 MiB of scratch per q, so
+    # systems of the Nk=64 crystal (NI = 256, 48 bosonic frequencies): 96 MiB of scratch per q, so
     # three q points take two passes over the 128 MiB array
     cr = gi.make_crystal(91, 8, 4, 2, 256, 50.0, qlist=[1, 3, 5])
     gr = gi.make_grid(50.0, 48, 48, 48, ncont=16)
