@@ -233,7 +233,7 @@ def main():
         mlp, mlp_hist = learned.trained_seed(args.omega, device=local)
     ctx = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)
     eps = torch.from_numpy(cr.eps).cuda()
-    chain = Chain(ctx, eps, prec=prec, qb=8, iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
+    chain = Chain(ctx, eps, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
     fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, gr.ntau)
     flops_step = (fp + fs) * nq
 
@@ -257,12 +257,14 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed steps only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         one_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -308,7 +310,7 @@ def main():
         for _ in range(args.e2e_steps):
             ctx2 = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)   # M generated from the seed
             eps_d = eps_h.to("cuda", non_blocking=True)
-            ch = Chain(ctx2, eps_d, prec=prec, qb=8, iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
+            ch = Chain(ctx2, eps_d, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
             ch.start_g0()
             ch.sigma()
             if world > 1:

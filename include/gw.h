@@ -46,7 +46,8 @@ typedef enum {
 typedef enum {
   GW_FP64 = 0,    /* native FP64 (CUDA cores); the parity path */
   GW_FP16X2 = 1,  /* tcgen05 tensor cores: fp16 hi/lo split operands, 3 products, FP32 TMEM accumulation */
-  GW_BF16X3 = 2   /* tcgen05 tensor cores: bf16 three-slice split, 6 products, FP32 TMEM accumulation */
+  GW_BF16X3 = 2,  /* tcgen05 tensor cores: bf16 three-slice split, 6 products, FP32 TMEM accumulation */
+  GW_F32X2 = 3    /* float-float on the FP32 pipes: each value hi + lo in two FP32 (~44-bit significand) */
 } gw_prec;
 
 typedef enum { GW_BOSE = 0, GW_FERMI = 1 } gw_stat;
@@ -132,14 +133,18 @@ gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, c
                          double* out);
 
 /* Screened interaction minus bare Coulomb, W~ = W - v (Sec. III.B.3), at the bosonic
- * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2,
- * solve (1 - Pi) X = Pi by LU without pivoting (1 - Pi has Hermitian part >= 1),
- * W~ = v^1/2 X v^1/2, for the nqb q points iq0 .. iq0 + nqb - 1 at once.
+ * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2, X = (1 - Pi)^-1 Pi,
+ * W~ = v^1/2 X v^1/2, for the nqb q points iq0 .. iq0 + nqb - 1 at once. With ni a
+ * multiple of 32 (ni <= 320) X = (1 - Pi)^-1 - 1 from a blocked in-place Gauss-Jordan
+ * inversion; otherwise by elimination of [1 - Pi | Pi] (GW_FP64 only). No pivoting:
+ * 1 - Pi has Hermitian part >= 1.
+ * prec: GW_FP64 (native FP64) or GW_F32X2 (float-float arithmetic, the mixed-precision
+ * chain's choice; relative error ~1e-12 per element); else GW_EUNSUPPORTED.
  * P_iv, Wt_iv cplx [nqb][nnu][ni][ni]; info out (device) [nqb][nnu]: 0, or j+1 for a
  * zero pivot at elimination step j (that system's output is then undefined).
  * Uses nqb * nnu * ni * 2 ni * 16 bytes of workspace that the context allocates
  * (and grows) on first use. */
-gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, double* Wt_iv, int* info);
+gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, gw_prec prec, double* Wt_iv, int* info);
 
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgw.so")
 
 GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ESINGULAR, GW_ENOCONV, GW_ETIMEOUT, GW_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-GW_FP64, GW_FP16X2, GW_BF16X3 = 0, 1, 2
+GW_FP64, GW_FP16X2, GW_BF16X3, GW_F32X2 = 0, 1, 2, 3
 GW_BOSE, GW_FERMI = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU, GW_TAU_TO_IW_CONT = 0, 1, 2
 GW_PADE, GW_CPE = 0, 1
@@ -101,7 +101,7 @@ def load_library(path=LIB_PATH):
         "gw_green_tau": [vp, vp, vp, vp, vp, vp, vp],
         "gw_polarization": [vp, i32, vp, i32, vp],
         "gw_tau_to_freq": [vp, i32, i32, i64, vp, vp],
-        "gw_screen": [vp, i32, i32, vp, vp, vp],
+        "gw_screen": [vp, i32, i32, vp, i32, vp, vp],
         "gw_selfenergy": [vp, i32, vp, vp, vp, i32, vp, vp],
         "gw_continue": [vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp],
         "gw_cpe_setup": [vp, i32, ctypes.POINTER(dbl), dbl],
@@ -219,8 +219,8 @@ class GW:
         self._check(self.lib.gw_tau_to_freq(self.h, int(stat), int(direction), int(batch), _ptr(x), _ptr(y)),
                     "gw_tau_to_freq")
 
-    def screen(self, iq0, nqb, P_iv, W_iv, info):
-        self._check(self.lib.gw_screen(self.h, iq0, nqb, _ptr(P_iv), _ptr(W_iv), _ptr(info)), "gw_screen")
+    def screen(self, iq0, nqb, P_iv, W_iv, info, prec=GW_FP64):
+        self._check(self.lib.gw_screen(self.h, iq0, nqb, _ptr(P_iv), int(prec), _ptr(W_iv), _ptr(info)), "gw_screen")
 
     def selfenergy(self, iq, G, occ, W_tau, S, Sx=None, prec=GW_FP64):
         self._check(self.lib.gw_selfenergy(self.h, iq, _ptr(G), _ptr(occ), _ptr(W_tau), int(prec), _ptr(S),

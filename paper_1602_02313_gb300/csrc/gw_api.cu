@@ -523,7 +523,7 @@ gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, con
   return launch_transform(c, (int)stat, (int)dir, batch, in, out);
 }
 
-gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W, int* info) {
+gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, gw_prec prec, double* W, int* info) {
   if (!c || !P || !W || !info || iq0 < 0 || nqb < 1 || iq0 + nqb > c->nq) return GW_EINVAL;
   const size_t need = (size_t)nqb * c->nnu * c->ni * 2 * c->ni * sizeof(double2);
   if (need > c->aug_bytes) {
@@ -536,7 +536,7 @@ gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W, int
     }
     c->aug_bytes = need;
   }
-  return launch_screen(c, iq0, nqb, P, W, info, c->d_aug);
+  return launch_screen(c, iq0, nqb, (int)prec, P, W, info, c->d_aug);
 }
 
 gw_status gw_selfenergy(gw_ctx* c, int iq, const double* G, const double* occ, const double* W, gw_prec prec,

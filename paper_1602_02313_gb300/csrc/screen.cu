@@ -105,66 +105,160 @@ __global__ void __launch_bounds__(512) k_screen(const double2* __restrict__ P, c
   if (threadIdx.x == 0) info[sys] = 0;
 }
 
-// Blocked Gauss-Jordan form of the same solve, one thread block per system:
-// for each 32-column block row R: invert the pivot block A[R][R] in shared memory,
-// U = A[R][R]^-1 A[R][c > R] (c running over the remaining left columns and all right-hand
-// columns), then A[i][c] -= A[i][R] U for every row i outside R. The rank-32 updates are
-// register-tiled FP64 products (8 rows x 4 columns per thread) fed from shared memory, so
-// the augmented matrix is read and written once per block row instead of once per column.
-// Work 1.5 ni^3 complex multiply-adds.
+// Blocked in-place Gauss-Jordan inversion, one thread block per system. Since
+// Pi = 1 - A with A = 1 - Pi, the solution of A X = Pi is X = A^-1 - 1, so only A^-1 is
+// formed (ni^3 complex multiply-adds instead of the 1.5 ni^3 of eliminating [A | Pi]).
+// For each 32-row block R: invert the pivot block A_RR in shared memory (no pivoting),
+// U_c = A_RR^-1 A_Rc for every column block c != R, A_ic -= A_iR U_c for every row i
+// outside R, A_iR <- -A_iR A_RR^-1 and A_RR <- A_RR^-1. The rank-32 updates are
+// register-tiled (8 rows x 4 columns per thread) from shared memory, so the matrix is
+// read and written once per block row.
+//
+// Two arithmetic policies share the kernel:
+//  * Fp64 : double2 values, FP64 fused multiply-adds;
+//  * Ff32 : float-float values (hi + lo, two FP32 each, ~44-bit significand). A product
+//           is hi*hi with its exact rounding error from an FMA plus the two cross terms;
+//           it joins the accumulator through an error-free two-sum, the errors collect in
+//           the accumulator's low word. All of it runs on the FP32 pipes, which on this GPU
+//           issue far more operations per clock than the FP64 ones.
 constexpr int GJ_B = 32;
-constexpr int GJ_CH = 32;  // columns per update sub-chunk
 
-__global__ void __launch_bounds__(256, 1) k_screen_gj(const double2* __restrict__ P, const double* __restrict__ sqrtv,
-                                                     int nnu, int ni, double2* __restrict__ aug_all,
-                                                     double2* __restrict__ W, int* __restrict__ info) {
-  extern __shared__ double2 gsm[];
-  double2* Pinv = gsm;                    // [32][33]
-  double2* L = Pinv + GJ_B * (GJ_B + 1);  // [ni][33]: A[i][R] for all rows (rows of R zeroed)
-  double2* U = L + ni * (GJ_B + 1);       // [32][GJ_CH + 1]
+struct Fp64 {
+  using S = double2;    // stored value (workspace, shared memory)
+  using Acc = double2;  // accumulator
+  __device__ static S from(double re, double im) { return make_double2(re, im); }
+  __device__ static double2 to(S v) { return v; }
+  __device__ static S zero() { return make_double2(0.0, 0.0); }
+  __device__ static Acc azero() { return make_double2(0.0, 0.0); }
+  __device__ static bool is_zero(S v) { return v.x == 0.0 && v.y == 0.0; }
+  __device__ static void mac(Acc& a, S l, S u) {  // a += l u
+    a.x = fma(l.x, u.x, fma(-l.y, u.y, a.x));
+    a.y = fma(l.x, u.y, fma(l.y, u.x, a.y));
+  }
+  __device__ static S val(Acc a) { return a; }
+  __device__ static S sub(S b, Acc a) { return make_double2(b.x - a.x, b.y - a.y); }  // b - a
+  __device__ static S inv(S v) { return cinv(v); }
+};
+
+struct Ff32 {
+  struct __align__(16) S {
+    float rh, rl, ih, il;
+  };
+  using Acc = S;
+  __device__ static S from(double re, double im) {
+    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+    return {rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih)};
+  }
+  __device__ static double2 to(S v) {
+    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+  }
+  __device__ static S zero() { return {0.f, 0.f, 0.f, 0.f}; }
+  __device__ static Acc azero() { return {0.f, 0.f, 0.f, 0.f}; }
+  __device__ static bool is_zero(S v) { return v.rh == 0.f && v.ih == 0.f; }
+  // h + l += (xh + xl)(yh + yl), dropping xl yl
+  __device__ __forceinline__ static void ffmac(float& h, float& l, float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    float e = fmaf(xh, yh, -p);
+    e = fmaf(xh, yl, e);
+    e = fmaf(xl, yh, e);
+    const float s = h + p;
+    const float v = s - h;
+    const float err = (h - (s - v)) + (p - v);
+    h = s;
+    l += err + e;
+  }
+  __device__ static void mac(Acc& a, S x, S y) {
+    ffmac(a.rh, a.rl, x.rh, x.rl, y.rh, y.rl);
+    ffmac(a.rh, a.rl, -x.ih, -x.il, y.ih, y.il);
+    ffmac(a.ih, a.il, x.rh, x.rl, y.ih, y.il);
+    ffmac(a.ih, a.il, x.ih, x.il, y.rh, y.rl);
+  }
+  __device__ __forceinline__ static void renorm(float& h, float& l) {
+    const float s = h + l;
+    l = l - (s - h);
+    h = s;
+  }
+  __device__ static S val(Acc a) {
+    renorm(a.rh, a.rl);
+    renorm(a.ih, a.il);
+    return a;
+  }
+  __device__ __forceinline__ static void ffsub(float bh, float bl, float ah, float al, float& h, float& l) {
+    const float s = bh - ah;
+    const float v = s - bh;
+    const float err = (bh - (s - v)) + (-ah - v);
+    h = s;
+    l = err + (bl - al);
+    renorm(h, l);
+  }
+  __device__ static S sub(S b, Acc a) {
+    S r;
+    ffsub(b.rh, b.rl, a.rh, a.rl, r.rh, r.rl);
+    ffsub(b.ih, b.il, a.ih, a.il, r.ih, r.il);
+    return r;
+  }
+  __device__ static S inv(S v) {  // one reciprocal per pivot: in FP64
+    const double2 d = to(v);
+    const double2 r = cinv(d);
+    return from(r.x, r.y);
+  }
+};
+
+template <class AR>
+__global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict__ P, const double* __restrict__ sqrtv,
+                                                      int nnu, int ni, typename AR::S* __restrict__ work,
+                                                      double2* __restrict__ W, int* __restrict__ info) {
+  using S = typename AR::S;
+  using Acc = typename AR::Acc;
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  S* Pinv = reinterpret_cast<S*>(gsm_raw);  // [32][33]
+  S* L = Pinv + GJ_B * (GJ_B + 1);           // [ni][33]: A[i][R] for all rows (rows of R zeroed)
+  S* U = L + (size_t)ni * (GJ_B + 1);        // [32][33]
   __shared__ int bad;
-  __shared__ double2 fcol[GJ_B], rowj[GJ_B];
+  __shared__ S fcol[GJ_B], rowj[GJ_B];
   const int sys = blockIdx.x;
   const int iqb = sys / nnu;
-  const int n2 = 2 * ni;
   const double* sv = sqrtv + (size_t)iqb * ni;
   const double2* Ps = P + (size_t)sys * ni * ni;
-  double2* A = aug_all + (size_t)sys * ni * n2;
+  S* A = work + (size_t)sys * ni * ni;
   const int t = threadIdx.x;
   if (t == 0) bad = 0;
   for (int e = t; e < ni * ni; e += blockDim.x) {
     const int I = e / ni, J = e % ni;
     const double s = sv[I] * sv[J];
     const double2 p = Ps[e];
-    const double2 pi = make_double2(s * p.x, s * p.y);
-    A[(size_t)I * n2 + J] = make_double2((I == J ? 1.0 : 0.0) - pi.x, -pi.y);
-    A[(size_t)I * n2 + ni + J] = pi;
+    A[e] = AR::from((I == J ? 1.0 : 0.0) - s * p.x, -s * p.y);
   }
   __syncthreads();
   const int tr = t & 31, tc = t >> 5;  // row lane, column group (8 groups x 4 columns)
   for (int k0 = 0; k0 < ni; k0 += GJ_B) {
-    // pivot block and the left block column of all rows
     for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
       const int r = e / GJ_B, c = e % GJ_B;
-      Pinv[r * (GJ_B + 1) + c] = A[(size_t)(k0 + r) * n2 + k0 + c];
+      Pinv[r * (GJ_B + 1) + c] = A[(size_t)(k0 + r) * ni + k0 + c];
     }
     for (int e = t; e < ni * GJ_B; e += blockDim.x) {
       const int r = e / GJ_B, c = e % GJ_B;
-      L[r * (GJ_B + 1) + c] = (r >= k0 && r < k0 + GJ_B) ? make_double2(0.0, 0.0) : A[(size_t)r * n2 + k0 + c];
+      L[r * (GJ_B + 1) + c] = (r >= k0 && r < k0 + GJ_B) ? AR::zero() : A[(size_t)r * ni + k0 + c];
     }
     __syncthreads();
     // in-place Gauss-Jordan inversion of the 32 x 32 pivot block (no pivoting):
     // row j <- row j / p (entry j -> 1/p); other rows r: a_rc -= a_rj a_jc / p, a_rj <- -a_rj / p
     for (int j = 0; j < GJ_B; ++j) {
-      const double2 p = Pinv[j * (GJ_B + 1) + j];
-      if (p.x == 0.0 && p.y == 0.0) {
+      const S p = Pinv[j * (GJ_B + 1) + j];
+      if (AR::is_zero(p)) {
         if (t == 0) bad = k0 + j + 1;
         break;
       }
-      const double2 ip = cinv(p);
+      const S ip = AR::inv(p);
       if (t < GJ_B) {
         fcol[t] = Pinv[t * (GJ_B + 1) + j];
-        rowj[t] = t == j ? ip : cmul(Pinv[j * (GJ_B + 1) + t], ip);
+        if (t == j) {
+          rowj[t] = ip;
+        } else {
+          Acc a = AR::azero();
+          AR::mac(a, Pinv[j * (GJ_B + 1) + t], ip);
+          rowj[t] = AR::val(a);
+        }
       }
       __syncthreads();
       for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
@@ -172,58 +266,53 @@ __global__ void __launch_bounds__(256, 1) k_screen_gj(const double2* __restrict_
         if (r == j) {
           Pinv[r * (GJ_B + 1) + c] = rowj[c];
         } else {
-          double2 a = c == j ? make_double2(0.0, 0.0) : Pinv[r * (GJ_B + 1) + c];
-          const double2 f = fcol[r], u = rowj[c];
-          a.x -= f.x * u.x - f.y * u.y;
-          a.y -= f.x * u.y + f.y * u.x;
-          Pinv[r * (GJ_B + 1) + c] = a;
+          Acc a = AR::azero();
+          AR::mac(a, fcol[r], rowj[c]);
+          Pinv[r * (GJ_B + 1) + c] = AR::sub(c == j ? AR::zero() : Pinv[r * (GJ_B + 1) + c], a);
         }
       }
       __syncthreads();
     }
     __syncthreads();
     if (bad) break;
-    // remaining columns in sub-chunks: U = Pinv A[R][chunk]; A[i][chunk] -= L[i] U
-    for (int c0 = k0 + GJ_B; c0 < n2; c0 += GJ_CH) {
-      const int cw = min(GJ_CH, n2 - c0);
-      for (int e = t; e < GJ_B * GJ_CH; e += blockDim.x) {
-        const int r = e / GJ_CH, c = e % GJ_CH;
-        double2 s = make_double2(0.0, 0.0);
-        if (c < cw) {
-          for (int j = 0; j < GJ_B; ++j) {
-            const double2 pv = Pinv[r * (GJ_B + 1) + j];
-            const double2 a = A[(size_t)(k0 + j) * n2 + c0 + c];
-            s.x += pv.x * a.x - pv.y * a.y;
-            s.y += pv.x * a.y + pv.y * a.x;
-          }
+    for (int c0 = 0; c0 < ni; c0 += GJ_B) {
+      const bool isR = c0 == k0;
+      // U = A_RR^-1 A_R,chunk (the pivot block inverse itself for the chunk R)
+      for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
+        const int r = e / GJ_B, c = e % GJ_B;
+        S u;
+        if (isR) {
+          u = Pinv[r * (GJ_B + 1) + c];
+        } else {
+          Acc a = AR::azero();
+          for (int j = 0; j < GJ_B; ++j) AR::mac(a, Pinv[r * (GJ_B + 1) + j], A[(size_t)(k0 + j) * ni + c0 + c]);
+          u = AR::val(a);
         }
-        U[r * (GJ_CH + 1) + c] = s;
+        U[r * (GJ_B + 1) + c] = u;
       }
       __syncthreads();
-      for (int e = t; e < GJ_B * GJ_CH; e += blockDim.x) {
-        const int r = e / GJ_CH, c = e % GJ_CH;
-        if (c < cw) A[(size_t)(k0 + r) * n2 + c0 + c] = U[r * (GJ_CH + 1) + c];
+      for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
+        const int r = e / GJ_B, c = e % GJ_B;
+        A[(size_t)(k0 + r) * ni + c0 + c] = U[r * (GJ_B + 1) + c];
       }
-      // rank-32 update of all rows outside R: thread (tr, tc) owns rows tr + 32 m, columns 4 tc .. 4 tc + 3
+      // rank-32 update of all rows outside R: thread (tr, tc) owns rows tr + 32 m, columns 4 tc .. 4 tc + 3;
+      // the chunk R starts from zero (A_iR <- -A_iR A_RR^-1)
       for (int rbase = 0; rbase < ni; rbase += 256) {
-        double2 acc[8][4];
+        Acc acc[8][4];
 #pragma unroll
         for (int m = 0; m < 8; ++m)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[m][q] = make_double2(0.0, 0.0);
+          for (int q = 0; q < 4; ++q) acc[m][q] = AR::azero();
         for (int j = 0; j < GJ_B; ++j) {
-          double2 uq[4];
+          S uq[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) uq[q] = U[j * (GJ_CH + 1) + 4 * tc + q];
+          for (int q = 0; q < 4; ++q) uq[q] = U[j * (GJ_B + 1) + 4 * tc + q];
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
             const int r = rbase + tr + 32 * m;
-            const double2 l = r < ni ? L[r * (GJ_B + 1) + j] : make_double2(0.0, 0.0);
+            const S l = r < ni ? L[r * (GJ_B + 1) + j] : AR::zero();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              acc[m][q].x = fma(l.x, uq[q].x, fma(-l.y, uq[q].y, acc[m][q].x));
-              acc[m][q].y = fma(l.x, uq[q].y, fma(l.y, uq[q].x, acc[m][q].y));
-            }
+            for (int q = 0; q < 4; ++q) AR::mac(acc[m][q], l, uq[q]);
           }
         }
 #pragma unroll
@@ -232,14 +321,8 @@ __global__ void __launch_bounds__(256, 1) k_screen_gj(const double2* __restrict_
           if (r >= ni || (r >= k0 && r < k0 + GJ_B)) continue;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const int c = 4 * tc + q;
-            if (c < cw) {
-              double2* a = &A[(size_t)r * n2 + c0 + c];
-              double2 v = *a;
-              v.x -= acc[m][q].x;
-              v.y -= acc[m][q].y;
-              *a = v;
-            }
+            S* a = &A[(size_t)r * ni + c0 + 4 * tc + q];
+            *a = AR::sub(isR ? AR::zero() : *a, acc[m][q]);
           }
         }
       }
@@ -250,29 +333,41 @@ __global__ void __launch_bounds__(256, 1) k_screen_gj(const double2* __restrict_
     if (t == 0) info[sys] = bad;
     return;
   }
+  // W~ = v^1/2 (A^-1 - 1) v^1/2
   double2* Ws = W + (size_t)sys * ni * ni;
   for (int e = t; e < ni * ni; e += blockDim.x) {
     const int I = e / ni, J = e % ni;
     const double s = sv[I] * sv[J];
-    const double2 x = A[(size_t)I * n2 + ni + J];
-    Ws[e] = make_double2(s * x.x, s * x.y);
+    const double2 x = AR::to(A[e]);
+    Ws[e] = make_double2(s * (x.x - (I == J ? 1.0 : 0.0)), s * x.y);
   }
   if (t == 0) info[sys] = 0;
 }
 
+template <class AR>
+gw_status launch_inv(gw_ctx* c, int iq0, int nsys, const double* P, double* W, int* info, double* aug) {
+  using S = typename AR::S;
+  const size_t smem = sizeof(S) * (GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1) + GJ_B * (GJ_B + 1));
+  cudaFuncSetAttribute(k_screen_inv<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_screen_inv<AR><<<nsys, 256, smem, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu,
+                                                   c->ni, reinterpret_cast<S*>(aug), (double2*)W, info);
+  return check_launch(c, "screen");
+}
+
 }  // namespace
 
-gw_status launch_screen(gw_ctx* c, int iq0, int nqb, const double* P, double* W, int* info, double* aug) {
+gw_status launch_screen(gw_ctx* c, int iq0, int nqb, int prec, const double* P, double* W, int* info, double* aug) {
   const int nsys = nqb * c->nnu;
-  const size_t smem = sizeof(double2) * (GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1) + GJ_B * (GJ_CH + 1));
-  if (c->ni % GJ_B == 0 && smem <= 200 * 1024) {
-    cudaFuncSetAttribute(k_screen_gj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_screen_gj<<<nsys, 256, smem, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu, c->ni,
-                                                 (double2*)aug, (double2*)W, info);
-  } else {
-    k_screen<<<nsys, 512, 0, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu, c->ni,
-                                          (double2*)aug, (double2*)W, info);
+  const size_t smem = sizeof(double2) * (2 * GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1));
+  const bool blocked = c->ni % GJ_B == 0 && smem <= 200 * 1024;
+  if (prec == GW_F32X2) {
+    if (!blocked) return set_err(c, GW_EUNSUPPORTED, "gw_screen: GW_F32X2 needs ni a multiple of 32 and ni <= 320");
+    return launch_inv<Ff32>(c, iq0, nsys, P, W, info, aug);
   }
+  if (prec != GW_FP64) return set_err(c, GW_EUNSUPPORTED, "gw_screen: precision must be GW_FP64 or GW_F32X2");
+  if (blocked) return launch_inv<Fp64>(c, iq0, nsys, P, W, info, aug);
+  k_screen<<<nsys, 512, 0, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu, c->ni,
+                                        (double2*)aug, (double2*)W, info);
   return check_launch(c, "screen");
 }
 

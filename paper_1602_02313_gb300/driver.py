@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (GW_BOSE, GW_CPE, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
+from . import (GW_BOSE, GW_CPE, GW_F32X2, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
                GW_TAU_TO_IW_CONT, GwError)
 
 
@@ -39,12 +39,16 @@ class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
     def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-5, mlp=None,
-                 nfit=64):
+                 nfit=64, screen_prec=None):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
         self.nnu, self.nw, self.ncont = len(g.nu_idx), len(g.w_idx), g.ncont
         self.prec = prec
+        # the dielectric solve: native FP64 on the FP64 chain, float-float on the mixed one
+        if screen_prec is None:
+            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 or ctx.cr.ni > 320 else GW_F32X2
+        self.screen_prec = screen_prec
         self.iqs = list(range(cr.nq)) if iqs is None else list(iqs)
         self.qb = max(1, min(qb, len(self.iqs)))
         self.cont_method = cont_method
@@ -110,7 +114,8 @@ class Chain:
             for j, iq in enumerate(batch):
                 self._timed("polarization", lambda: ctx.polarization(iq, G, self.P[j], self.prec))
                 ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j])
-            ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)])
+            ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)],
+                       self.screen_prec)
             for j, iq in enumerate(batch):
                 ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt)
                 self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))

@@ -13,6 +13,7 @@ import oracle as orc
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_F32X2 = 1e-11  # float-float dielectric solve (~44-bit significand); measured 5e-14 at NI = 256
 
 
 @pytest.fixture(scope="module")
@@ -142,6 +143,48 @@ def test_screen(gw, case):
     assert np.all(host(info) == 0)
     for iq in range(cr.nq):
         assert rel(host(W)[iq], orc.screen(P[iq], cr.v[iq])) < TOL
+    if cr.ni % 32 == 0:
+        # float-float arithmetic on the same systems
+        ctx.screen(0, cr.nq, dev(P), W, info, gw.GW_F32X2)
+        ctx.sync()
+        assert np.all(host(info) == 0)
+        for iq in range(cr.nq):
+            assert rel(host(W)[iq], orc.screen(P[iq], cr.v[iq])) < TOL_F32X2
+
+
+def _screen_systems(ni, nnu, seed):
+    """Hermitian negative semidefinite P(i nu) with the Coulomb weights of the generator, scaled so
+    that the largest eigenvalue of -Pi is 20 at the first frequency and falls off as 1 / (1 + j)."""
+    rng = np.random.default_rng(seed)
+    g = rng.uniform(0.0, 3.0, ni)
+    v = 4.0 * np.pi / (0.05 + g * g)
+    sv = np.sqrt(v)
+    P = np.empty((nnu, ni, ni), complex)
+    for j in range(nnu):
+        B = (rng.standard_normal((ni, ni)) + 1j * rng.standard_normal((ni, ni))) / np.sqrt(2 * ni)
+        Pj = -(B @ B.conj().T)
+        Pi = sv[:, None] * Pj * sv[None, :]
+        lam = np.linalg.eigvalsh(-Pi).max()
+        P[j] = Pj * (20.0 / (1.0 + j)) / lam
+    return P, v
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
+def test_screen_full_size(gw, prec):
+    """One q point's 48 systems at NI = 256 (the benchmarked crystal's size), both arithmetics."""
+    cr, gr = gi.make_config("nk64_nb64", qlist=[0], nk=8)
+    P, v = _screen_systems(cr.ni, gr.nnu, 77)
+    cr.v[0] = v
+    ctx = gw.GW(gr, cr, omega=0.7)
+    W = zeros((1,) + P.shape, "c16")
+    info = zeros((1, gr.nnu), "i4")
+    ctx.screen(0, 1, dev(P[None]), W, info, gw.GW_FP64 if prec == "fp64" else gw.GW_F32X2)
+    ctx.sync()
+    assert np.all(host(info) == 0)
+    ref = orc.screen(P, v)
+    err = rel(host(W)[0], ref)
+    print(f"screen NI=256 {prec}: rel err {err:.2e}")
+    assert err < (TOL if prec == "fp64" else TOL_F32X2)
 
 
 # ------------------------------------------------------------------ self-energy
