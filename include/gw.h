@@ -122,7 +122,10 @@ gw_status gw_green_tau(gw_ctx* ctx, const double* eps, const double* sigx, const
 gw_status gw_polarization(gw_ctx* ctx, int iq, const double* G_tau, gw_prec prec, double* P_tau);
 
 /* Imaginary time <-> Matsubara transforms (Eq. trans and its bosonic / inverse
- * counterparts), fixed FP64 matrices applied as batched matvecs.
+ * counterparts), fixed matrices (built in extended precision, stored FP64) applied as
+ * batched matvecs. prec: GW_FP64 (native FP64), or GW_F32X2 for the two bosonic
+ * directions (float-float arithmetic, relative error ~1e-13; the mixed chain's choice);
+ * anything else returns GW_EUNSUPPORTED.
  *  BOSE  TAU_TO_IW : in cplx [ntau][batch]        -> out cplx [nnu][batch]
  *  BOSE  IW_TO_TAU : in cplx [nnu][m][m] of a Hermitian-matrix function (batch = m)
  *                    -> out cplx [ntau][m][m]; uses W(-i nu) = W(i nu)^dagger
@@ -130,7 +133,7 @@ gw_status gw_polarization(gw_ctx* ctx, int iq, const double* G_tau, gw_prec prec
  *  FERMI TAU_TO_IW_CONT : in real [batch][ntau]   -> out cplx [batch][ncont]
  *  FERMI IW_TO_TAU : in cplx [batch][nw] of a real tau-function -> out real [batch][ntau] */
 gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, const double* in,
-                         double* out);
+                         gw_prec prec, double* out);
 
 /* Screened interaction minus bare Coulomb, W~ = W - v (Sec. III.B.3), at the bosonic
  * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2, X = (1 - Pi)^-1 Pi,

@@ -100,7 +100,7 @@ def load_library(path=LIB_PATH):
         "gw_destroy": [vp], "gw_sync": [vp], "gw_last_error": [vp],
         "gw_green_tau": [vp, vp, vp, vp, vp, vp, vp],
         "gw_polarization": [vp, i32, vp, i32, vp],
-        "gw_tau_to_freq": [vp, i32, i32, i64, vp, vp],
+        "gw_tau_to_freq": [vp, i32, i32, i64, vp, i32, vp],
         "gw_screen": [vp, i32, i32, vp, i32, vp, vp],
         "gw_selfenergy": [vp, i32, vp, vp, vp, i32, vp, vp],
         "gw_continue": [vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp],
@@ -215,9 +215,9 @@ class GW:
     def polarization(self, iq, G, P, prec=GW_FP64):
         self._check(self.lib.gw_polarization(self.h, iq, _ptr(G), int(prec), _ptr(P)), "gw_polarization")
 
-    def tau_to_freq(self, stat, direction, batch, x, y):
-        self._check(self.lib.gw_tau_to_freq(self.h, int(stat), int(direction), int(batch), _ptr(x), _ptr(y)),
-                    "gw_tau_to_freq")
+    def tau_to_freq(self, stat, direction, batch, x, y, prec=GW_FP64):
+        self._check(self.lib.gw_tau_to_freq(self.h, int(stat), int(direction), int(batch), _ptr(x), int(prec),
+                                            _ptr(y)), "gw_tau_to_freq")
 
     def screen(self, iq0, nqb, P_iv, W_iv, info, prec=GW_FP64):
         self._check(self.lib.gw_screen(self.h, iq0, nqb, _ptr(P_iv), int(prec), _ptr(W_iv), _ptr(info)), "gw_screen")

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <string>
 
+#include "arith.cuh"
 #include "gw_internal.h"
 
 namespace gwi {
@@ -153,70 +154,68 @@ gw_status launch_dyson(gw_ctx* c, const double* eps, const double* sigx, const d
 // ----------------------------------------------------------------------------
 // Transforms: fixed FP64 matrices applied as batched matvecs.
 // ----------------------------------------------------------------------------
-// BOSE tau -> i nu: out[j][b] = sum_i T[j][i] in[i][b]  (complex T, complex data)
-template <int JB>
+// BOSE tau -> i nu: out[j][b] = sum_i T[j][i] in[i][b]  (complex T, complex data).
+// The arithmetic is a policy: FP64, or float-float (arith.cuh) on the FP32 pipes.
+template <int JB, class AR>
 __global__ void k_bose_fwd(const double2* __restrict__ T, const double2* __restrict__ in, double2* __restrict__ out,
                            int64_t batch, int ntau, int nf) {
-  extern __shared__ double2 sT[];
-  for (int i = threadIdx.x; i < nf * ntau; i += blockDim.x) sT[i] = T[i];
+  using S = typename AR::S;
+  extern __shared__ __align__(16) unsigned char bfsm[];
+  S* sT = reinterpret_cast<S*>(bfsm);
+  for (int i = threadIdx.x; i < nf * ntau; i += blockDim.x) sT[i] = AR::from(T[i].x, T[i].y);
   __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= batch) return;
   for (int j0 = 0; j0 < nf; j0 += JB) {
-    double2 acc[JB];
+    typename AR::Acc acc[JB];
 #pragma unroll
-    for (int q = 0; q < JB; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int q = 0; q < JB; ++q) acc[q] = AR::azero();
     for (int i = 0; i < ntau; ++i) {
-      const double2 x = in[(size_t)i * batch + b];
+      const double2 xd = in[(size_t)i * batch + b];
+      const S x = AR::from(xd.x, xd.y);
 #pragma unroll
-      for (int q = 0; q < JB; ++q) {
-        if (j0 + q < nf) {
-          const double2 t = sT[(j0 + q) * ntau + i];
-          acc[q].x = fma(t.x, x.x, fma(-t.y, x.y, acc[q].x));
-          acc[q].y = fma(t.x, x.y, fma(t.y, x.x, acc[q].y));
-        }
-      }
+      for (int q = 0; q < JB; ++q)
+        if (j0 + q < nf) AR::mac(acc[q], sT[(j0 + q) * ntau + i], x);
     }
 #pragma unroll
     for (int q = 0; q < JB; ++q)
-      if (j0 + q < nf) out[(size_t)(j0 + q) * batch + b] = acc[q];
+      if (j0 + q < nf) out[(size_t)(j0 + q) * batch + b] = AR::to(AR::val(acc[q]));
   }
 }
 
 // BOSE i nu -> tau of a Hermitian-matrix function W[j][I][J]:
 // ghat = (W_IJ + W_JI)/2 (transform of Re W(tau)), hhat = (W_IJ - W_JI)/(2i) (of Im W(tau));
 // Re W(tau_i) = sum_j A_ij Re ghat_j + B_ij Im ghat_j, Im W(tau_i) likewise with hhat.
+template <int IB, class AR>
 __global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W, double2* __restrict__ out,
                            int m, int ntau, int nf) {
-  extern __shared__ double sTb[];
-  for (int i = threadIdx.x; i < ntau * 2 * nf; i += blockDim.x) sTb[i] = Tb[i];
+  using S = typename AR::S;
+  using R = typename AR::R;
+  extern __shared__ __align__(16) unsigned char bbsm[];
+  R* sTb = reinterpret_cast<R*>(bbsm);
+  for (int i = threadIdx.x; i < ntau * 2 * nf; i += blockDim.x) sTb[i] = AR::rfrom(Tb[i]);
   __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t mm = (int64_t)m * m;
   if (e >= mm) return;
   const int I = (int)(e / m), J = (int)(e % m);
   const int64_t et = (int64_t)J * m + I;
-  for (int i0 = 0; i0 < ntau; i0 += 8) {
-    double gr[8], gi[8];
+  for (int i0 = 0; i0 < ntau; i0 += IB) {
+    typename AR::Acc acc[IB];  // re: Re W(tau), im: Im W(tau)
 #pragma unroll
-    for (int q = 0; q < 8; ++q) gr[q] = gi[q] = 0.0;
+    for (int q = 0; q < IB; ++q) acc[q] = AR::azero();
     for (int j = 0; j < nf; ++j) {
-      const double2 a = W[(size_t)j * mm + e], b = W[(size_t)j * mm + et];
-      const double ghr = 0.5 * (a.x + b.x), ghi = 0.5 * (a.y + b.y);
-      // (a - b)/(2i) = (a.y - b.y)/2 - i (a.x - b.x)/2
-      const double hhr = 0.5 * (a.y - b.y), hhi = -0.5 * (a.x - b.x);
+      const double2 ad = W[(size_t)j * mm + e], bd = W[(size_t)j * mm + et];
+      const S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
+      const S g = AR::half(AR::add(a, bv));
+      const S h = AR::mul_mi(AR::half(AR::dif(a, bv)));
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (i0 + q < ntau) {
-          const double A = sTb[(i0 + q) * 2 * nf + j], B = sTb[(i0 + q) * 2 * nf + nf + j];
-          gr[q] = fma(A, ghr, fma(B, ghi, gr[q]));
-          gi[q] = fma(A, hhr, fma(B, hhi, gi[q]));
-        }
-      }
+      for (int q = 0; q < IB; ++q)
+        if (i0 + q < ntau) AR::rmac2(acc[q], sTb[(i0 + q) * 2 * nf + j], sTb[(i0 + q) * 2 * nf + nf + j], g, h);
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      if (i0 + q < ntau) out[(size_t)(i0 + q) * mm + e] = make_double2(gr[q], gi[q]);
+    for (int q = 0; q < IB; ++q)
+      if (i0 + q < ntau) out[(size_t)(i0 + q) * mm + e] = AR::to(AR::val(acc[q]));
   }
 }
 
@@ -256,23 +255,40 @@ __global__ void k_fermi_bwd(const double* __restrict__ Tb, const double2* __rest
   out[e] = s;
 }
 
-gw_status launch_transform(gw_ctx* c, int stat, int dir, int64_t batch, const double* in, double* out) {
+gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch, const double* in, double* out) {
   const int nt = c->ntau;
   if (stat == GW_BOSE && dir == GW_TAU_TO_IW) {
-    const size_t sm = sizeof(double2) * c->nnu * nt;
     const int64_t blocks = (batch + 127) / 128;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_bose_fwd<8><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd, (const double2*)in,
-                                                           (double2*)out, batch, nt, c->nnu);
+    if (prec == GW_F32X2) {
+      const size_t sm = sizeof(arith::Ff32::S) * c->nnu * nt;
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_fwd<16, arith::Ff32><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
+                                                                             (const double2*)in, (double2*)out, batch,
+                                                                             nt, c->nnu);
+    } else {
+      const size_t sm = sizeof(double2) * c->nnu * nt;
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_fwd<8, arith::Fp64><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
+                                                                            (const double2*)in, (double2*)out, batch,
+                                                                            nt, c->nnu);
+    }
     return check_launch(c, "bose_fwd");
   }
   if (stat == GW_BOSE && dir == GW_IW_TO_TAU) {
     const int m = (int)batch;
-    const size_t sm = sizeof(double) * nt * 2 * c->nnu;
     const int64_t mm = (int64_t)m * m;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_bose_bwd<<<(unsigned)((mm + 127) / 128), 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m,
-                                                                      nt, c->nnu);
+    const unsigned blocks = (unsigned)((mm + 127) / 128);
+    if (prec == GW_F32X2) {
+      const size_t sm = sizeof(arith::Ff32::R) * nt * 2 * c->nnu;
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_bwd<16, arith::Ff32><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m, nt,
+                                                                   c->nnu);
+    } else {
+      const size_t sm = sizeof(double) * nt * 2 * c->nnu;
+      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_bwd<8, arith::Fp64><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m, nt,
+                                                                  c->nnu);
+    }
     return check_launch(c, "bose_bwd");
   }
   if (stat == GW_FERMI && (dir == GW_TAU_TO_IW || dir == GW_TAU_TO_IW_CONT)) {
@@ -517,10 +533,13 @@ gw_status gw_polarization(gw_ctx* c, int iq, const double* G, gw_prec prec, doub
   return GW_EINVAL;
 }
 
-gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, const double* in, double* out) {
+gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, const double* in, gw_prec prec,
+                         double* out) {
   if (!c || !in || !out || batch <= 0) return GW_EINVAL;
   if (stat == GW_BOSE && dir == GW_TAU_TO_IW_CONT) return GW_EINVAL;
-  return launch_transform(c, (int)stat, (int)dir, batch, in, out);
+  if (prec != GW_FP64 && !(prec == GW_F32X2 && stat == GW_BOSE))
+    return set_err(c, GW_EUNSUPPORTED, "gw_tau_to_freq: GW_FP64, or GW_F32X2 for the bosonic transforms");
+  return launch_transform(c, (int)stat, (int)dir, (int)prec, batch, in, out);
 }
 
 gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, gw_prec prec, double* W, int* info) {

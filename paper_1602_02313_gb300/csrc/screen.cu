@@ -11,6 +11,7 @@
 #include <mutex>
 #include <string>
 
+#include "arith.cuh"
 #include "gw_internal.h"
 
 namespace gwi {
@@ -114,95 +115,11 @@ __global__ void __launch_bounds__(512) k_screen(const double2* __restrict__ P, c
 // register-tiled (8 rows x 4 columns per thread) from shared memory, so the matrix is
 // read and written once per block row.
 //
-// Two arithmetic policies share the kernel:
-//  * Fp64 : double2 values, FP64 fused multiply-adds;
-//  * Ff32 : float-float values (hi + lo, two FP32 each, ~44-bit significand). A product
-//           is hi*hi with its exact rounding error from an FMA plus the two cross terms;
-//           it joins the accumulator through an error-free two-sum, the errors collect in
-//           the accumulator's low word. All of it runs on the FP32 pipes, which on this GPU
-//           issue far more operations per clock than the FP64 ones.
+// The arithmetic is a policy (arith.cuh): native FP64, or float-float on the FP32 pipes.
 constexpr int GJ_B = 32;
 
-struct Fp64 {
-  using S = double2;    // stored value (workspace, shared memory)
-  using Acc = double2;  // accumulator
-  __device__ static S from(double re, double im) { return make_double2(re, im); }
-  __device__ static double2 to(S v) { return v; }
-  __device__ static S zero() { return make_double2(0.0, 0.0); }
-  __device__ static Acc azero() { return make_double2(0.0, 0.0); }
-  __device__ static bool is_zero(S v) { return v.x == 0.0 && v.y == 0.0; }
-  __device__ static void mac(Acc& a, S l, S u) {  // a += l u
-    a.x = fma(l.x, u.x, fma(-l.y, u.y, a.x));
-    a.y = fma(l.x, u.y, fma(l.y, u.x, a.y));
-  }
-  __device__ static S val(Acc a) { return a; }
-  __device__ static S sub(S b, Acc a) { return make_double2(b.x - a.x, b.y - a.y); }  // b - a
-  __device__ static S inv(S v) { return cinv(v); }
-};
-
-struct Ff32 {
-  struct __align__(16) S {
-    float rh, rl, ih, il;
-  };
-  using Acc = S;
-  __device__ static S from(double re, double im) {
-    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
-    return {rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih)};
-  }
-  __device__ static double2 to(S v) {
-    return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
-  }
-  __device__ static S zero() { return {0.f, 0.f, 0.f, 0.f}; }
-  __device__ static Acc azero() { return {0.f, 0.f, 0.f, 0.f}; }
-  __device__ static bool is_zero(S v) { return v.rh == 0.f && v.ih == 0.f; }
-  // h + l += (xh + xl)(yh + yl), dropping xl yl
-  __device__ __forceinline__ static void ffmac(float& h, float& l, float xh, float xl, float yh, float yl) {
-    const float p = xh * yh;
-    float e = fmaf(xh, yh, -p);
-    e = fmaf(xh, yl, e);
-    e = fmaf(xl, yh, e);
-    const float s = h + p;
-    const float v = s - h;
-    const float err = (h - (s - v)) + (p - v);
-    h = s;
-    l += err + e;
-  }
-  __device__ static void mac(Acc& a, S x, S y) {
-    ffmac(a.rh, a.rl, x.rh, x.rl, y.rh, y.rl);
-    ffmac(a.rh, a.rl, -x.ih, -x.il, y.ih, y.il);
-    ffmac(a.ih, a.il, x.rh, x.rl, y.ih, y.il);
-    ffmac(a.ih, a.il, x.ih, x.il, y.rh, y.rl);
-  }
-  __device__ __forceinline__ static void renorm(float& h, float& l) {
-    const float s = h + l;
-    l = l - (s - h);
-    h = s;
-  }
-  __device__ static S val(Acc a) {
-    renorm(a.rh, a.rl);
-    renorm(a.ih, a.il);
-    return a;
-  }
-  __device__ __forceinline__ static void ffsub(float bh, float bl, float ah, float al, float& h, float& l) {
-    const float s = bh - ah;
-    const float v = s - bh;
-    const float err = (bh - (s - v)) + (-ah - v);
-    h = s;
-    l = err + (bl - al);
-    renorm(h, l);
-  }
-  __device__ static S sub(S b, Acc a) {
-    S r;
-    ffsub(b.rh, b.rl, a.rh, a.rl, r.rh, r.rl);
-    ffsub(b.ih, b.il, a.ih, a.il, r.ih, r.il);
-    return r;
-  }
-  __device__ static S inv(S v) {  // one reciprocal per pivot: in FP64
-    const double2 d = to(v);
-    const double2 r = cinv(d);
-    return from(r.x, r.y);
-  }
-};
+using arith::Fp64;
+using arith::Ff32;
 
 template <class AR>
 __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict__ P, const double* __restrict__ sqrtv,

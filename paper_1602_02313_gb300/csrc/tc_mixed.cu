@@ -268,7 +268,15 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   if (warp == 8) tmem_dealloc(tbase, 512);
 }
 
-// Sum the FP32 partial strips over K segments in FP64 and write the Hermitian P.
+// h + l += x with the rounding error of h + x kept exactly in l (Knuth's two-sum)
+__device__ __forceinline__ void two_sum_acc(float& h, float& l, float x) {
+  const float s = h + x;
+  const float v = s - h;
+  l += (h - (s - v)) + (x - v);
+  h = s;
+}
+
+// Sum the FP32 partial strips over K segments and write the Hermitian P (FP64).
 // One block per (32 x 32 block (ab, bb) with ab <= bb, tau); reads are coalesced along
 // the column, the mirrored lower triangle is written through a shared-memory transpose.
 __global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ part, int ni, int ntau,
@@ -288,24 +296,28 @@ __global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ pa
   const int4 sd = strips[strip];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int b = bb * 32 + tx;
-  double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
-  for (int s = 0; s < nseg; ++s) {
-    const int u = (s * nstrips + strip) * ntau + it;
-    const float* pre = part + (size_t)u * 2 * 128 * 256;
+  // float-float accumulators (hi + lo, error-free two-sum per addition): as exact as an FP64
+  // sum of these FP32 terms to ~2^-44, on the FP32 pipes (GB300's FP64 rate is ~1/64 of FP32)
+  float reh[4] = {0, 0, 0, 0}, rel[4] = {0, 0, 0, 0}, imh[4] = {0, 0, 0, 0}, iml[4] = {0, 0, 0, 0};
+  size_t o[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) o[r] = (size_t)((ab * 32 + ty + 8 * r) & 127) * 256 + (b - sd.y);
+  const size_t ustride = (size_t)nstrips * ntau * 2 * 128 * 256;  // one K segment further
+  const float* pre = part + ((size_t)strip * ntau + it) * 2 * 128 * 256;
+#pragma unroll 2
+  for (int s = 0; s < nseg; ++s, pre += ustride) {
     const float* pim = pre + 128 * 256;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const int a = ab * 32 + ty + 8 * r;
-      const size_t o = (size_t)(a & 127) * 256 + (b - sd.y);
-      re[r] += (double)pre[o];
-      im[r] += (double)pim[o];
+      two_sum_acc(reh[r], rel[r], pre[o[r]]);
+      two_sum_acc(imh[r], iml[r], pim[o[r]]);
     }
   }
   double2* Pt = P + (size_t)it * ni * ni;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int a = ab * 32 + ty + 8 * r;
-    double2 v = make_double2(re[r] * scale, im[r] * scale);
+    double2 v = make_double2(((double)reh[r] + (double)rel[r]) * scale, ((double)imh[r] + (double)iml[r]) * scale);
     if (a == b) v.y = 0.0;  // Im P_II = 0 exactly (the tensor-core sum leaves O(2^-22) residue)
     if (a < ni && b < ni && (ab < bb || a <= b)) Pt[(size_t)a * ni + b] = v;
     tr[ty + 8 * r][tx] = make_double2(v.x, -v.y);

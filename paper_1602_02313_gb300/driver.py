@@ -45,7 +45,8 @@ class Chain:
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
         self.nnu, self.nw, self.ncont = len(g.nu_idx), len(g.w_idx), g.ncont
         self.prec = prec
-        # the dielectric solve: native FP64 on the FP64 chain, float-float on the mixed one
+        # the dielectric solve and the bosonic transforms: native FP64 on the FP64 chain,
+        # float-float on the mixed one
         if screen_prec is None:
             screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 or ctx.cr.ni > 320 else GW_F32X2
         self.screen_prec = screen_prec
@@ -113,11 +114,11 @@ class Chain:
             batch = self.iqs[b0:b0 + self.qb]
             for j, iq in enumerate(batch):
                 self._timed("polarization", lambda: ctx.polarization(iq, G, self.P[j], self.prec))
-                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j])
+                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j], self.screen_prec)
             ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)],
                        self.screen_prec)
             for j, iq in enumerate(batch):
-                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt)
+                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt, self.screen_prec)
                 self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))
 
     def finish(self, vxc=None):

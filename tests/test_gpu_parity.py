@@ -13,6 +13,7 @@ import oracle as orc
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_F32X2_T = 1e-10  # float-float transforms (matrices with cancellation)
 TOL_F32X2 = 1e-11  # float-float dielectric solve (~44-bit significand); measured 5e-14 at NI = 256
 
 
@@ -116,6 +117,14 @@ def test_transforms(gw, case):
     ctx.tau_to_freq(gw.GW_BOSE, gw.GW_IW_TO_TAU, m, dev(W), Wt)
     ctx.sync()
     assert rel(host(Wt), orc.transforms.apply_bwd_hermitian(T["B_bwd_re"], T["B_bwd_im"], W)) < 1e-13
+    # float-float arithmetic (the mixed chain's bosonic transforms)
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_TAU_TO_IW, m * m, dev(x), y, gw.GW_F32X2)
+    ctx.tau_to_freq(gw.GW_BOSE, gw.GW_IW_TO_TAU, m, dev(W), Wt, gw.GW_F32X2)
+    ctx.sync()
+    e_fwd = rel(host(y), np.einsum("ji,iab->jab", T["B_fwd"], x))
+    e_bwd = rel(host(Wt), orc.transforms.apply_bwd_hermitian(T["B_bwd_re"], T["B_bwd_im"], W))
+    print(f"bosonic transforms in float-float: fwd {e_fwd:.1e}, bwd {e_bwd:.1e}")
+    assert e_fwd < TOL_F32X2_T and e_bwd < TOL_F32X2_T
     s = rng.standard_normal((29, gr.ntau))
     for d, key, nf in [(gw.GW_TAU_TO_IW, "F_fwd", gr.nw), (gw.GW_TAU_TO_IW_CONT, "F_cont", gr.ncont)]:
         o = zeros((29, nf), "c16")
