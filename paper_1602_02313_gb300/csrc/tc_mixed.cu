@@ -166,13 +166,46 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 
   if (warp < 8) {
     // ------------------------------------------------------------ producers
+    // X = w A for the strip's 128 rows: 512 items of (row, 8 pairs), two per thread. Within a
+    // warp, the 8 lanes of each quarter take rows r and r + 4 (r < 4 of an 8-row group), so
+    // their 16-byte stores land in 8 distinct bank groups of the 128-byte swizzle. The next
+    // chunk's operands and weights are loaded while the current chunk is written.
+    struct Item {
+      h8 rh, rl, ih, il;
+      float4 w0, w1;
+    };
+    int ir[2], ig[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int item = tid + 256 * j, ln = item & 31;
+      ir[j] = 8 * (item >> 5) + ((ln & 7) >> 2) * 4 + (ln >> 3);
+      ig[j] = ln & 3;
+    }
+    auto fetch = [&](int i, Item (&it2)[2]) {
+      const int g = g0 + i, k = g / cpk, c = g % cpk;
+      const __half* xh = YS + ys_tile(k, c, xb, 0, cpk, nib);
+      const __half* xl = YS + ys_tile(k, c, xb, 1, cpk, nib);
+      const float* wrow = wt + ((size_t)k * ntau + it) * npw + c * 32;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t oRe = sw128_off(ir[j], 8 * ig[j]), oIm = sw128_off(ir[j], 32 + 8 * ig[j]);
+        it2[j].rh = *reinterpret_cast<const h8*>(xh + oRe / 2);
+        it2[j].rl = *reinterpret_cast<const h8*>(xl + oRe / 2);
+        it2[j].ih = *reinterpret_cast<const h8*>(xh + oIm / 2);
+        it2[j].il = *reinterpret_cast<const h8*>(xl + oIm / 2);
+        it2[j].w0 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * ig[j]));
+        it2[j].w1 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * ig[j]) + 1);
+      }
+    };
+    Item cur[2], nxt[2];
+    if (nchunk > 0) fetch(0, cur);
     for (int i = 0; i < nchunk; ++i) {
       const int s = i & 1;
       if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
       unsigned char* st = base + s * P_STAGE_BYTES;
-      const int g = g0 + i, k = g / cpk, c = g % cpk;
       if (tid == 0) {
         // Y: rows [c0, c0 + N) = whole or leading parts of 128-row blocks, hi and lo slices
+        const int g = g0 + i, k = g / cpk, c = g % cpk;
         mbar_arrive_expect_tx(&S.full[s], 2 * ybytes_slice);
         for (int r0 = 0; r0 < N; r0 += 128) {
           const int rows = min(128, N - r0);
@@ -182,25 +215,17 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
                      (uint32_t)rows * 128, &S.full[s]);
         }
       }
-      // X = w A for the strip's 128 rows: 512 items of (row, 8 pairs)
-      const __half* xh = YS + ys_tile(k, c, xb, 0, cpk, nib);
-      const __half* xl = YS + ys_tile(k, c, xb, 1, cpk, nib);
-      const float* wrow = wt + ((size_t)k * ntau + it) * npw + c * 32;
-      for (int item = tid; item < 512; item += 256) {
-        const int r = item >> 2, gq = item & 3;
-        const uint32_t oRe = sw128_off(r, 8 * gq), oIm = sw128_off(r, 32 + 8 * gq);
-        const h8 rh = *reinterpret_cast<const h8*>(xh + oRe / 2);
-        const h8 rl = *reinterpret_cast<const h8*>(xl + oRe / 2);
-        const h8 ih = *reinterpret_cast<const h8*>(xh + oIm / 2);
-        const h8 il = *reinterpret_cast<const h8*>(xl + oIm / 2);
-        const float4 w0 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * gq));
-        const float4 w1 = __ldg(reinterpret_cast<const float4*>(wrow + 8 * gq) + 1);
-        const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+      if (i + 1 < nchunk) fetch(i + 1, nxt);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const uint32_t oRe = sw128_off(ir[j], 8 * ig[j]), oIm = sw128_off(ir[j], 32 + 8 * ig[j]);
+        const float wv[8] = {cur[j].w0.x, cur[j].w0.y, cur[j].w0.z, cur[j].w0.w,
+                             cur[j].w1.x, cur[j].w1.y, cur[j].w1.z, cur[j].w1.w};
         h8 orh, orl, oih, oil;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          split2(wv[e] * (__half2float(rh.v[e]) + __half2float(rl.v[e])), orh.v[e], orl.v[e]);
-          split2(wv[e] * (__half2float(ih.v[e]) + __half2float(il.v[e])), oih.v[e], oil.v[e]);
+          split2(wv[e] * (__half2float(cur[j].rh.v[e]) + __half2float(cur[j].rl.v[e])), orh.v[e], orl.v[e]);
+          split2(wv[e] * (__half2float(cur[j].ih.v[e]) + __half2float(cur[j].il.v[e])), oih.v[e], oil.v[e]);
         }
         *reinterpret_cast<h8*>(st + oRe) = orh;
         *reinterpret_cast<h8*>(st + oIm) = oih;
@@ -210,6 +235,8 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       fence_proxy_async_smem();
       mbar_arrive(&S.full[s]);
       if (S.abort_flag) break;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) cur[j] = nxt[j];
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
@@ -342,15 +369,22 @@ __device__ __forceinline__ size_t xs_tile(int k, int pblk, int kc, int sl, int n
   return ((((size_t)k * npb + pblk) * nkc + kc) * 4 + sl) * (size_t)(128 * 32);  // in halves
 }
 
-// Split M[q] into XS via a 32 x 32 shared-memory transpose (rows p >= nb^2 zero).
-__global__ void k_split_x(const double2* __restrict__ Mq, int ni, int np, int npb, __half* __restrict__ XS) {
+// Split M[q] into XS via a 32 x 32 shared-memory transpose (rows p >= nb^2 zero), and
+// write the epilogue's image XE[k][pblk][I][row] = 2^8 M (FP32 re, im; rows contiguous, so
+// that the 32 lanes of a warp, which own 32 consecutive rows, read 256 contiguous bytes).
+__global__ void k_split_x(const double2* __restrict__ Mq, int ni, int np, int npb, __half* __restrict__ XS,
+                          float2* __restrict__ XE) {
   __shared__ double2 tileS[32][33];
   const int k = blockIdx.z;
   const int p0 = blockIdx.x * 32, I0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   for (int r = ty; r < 32; r += 8) {
     const int I = I0 + r, p = p0 + tx;
-    tileS[r][tx] = (I < ni && p < np) ? Mq[((size_t)k * ni + I) * np + p] : make_double2(0.0, 0.0);
+    const double2 v = (I < ni && p < np) ? Mq[((size_t)k * ni + I) * np + p] : make_double2(0.0, 0.0);
+    tileS[r][tx] = v;
+    if (I < ni)
+      XE[(((size_t)k * npb + (p >> 7)) * ni + I) * 128 + (p & 127)] =
+          make_float2((float)(v.x * kScaleA), (float)(v.y * kScaleA));
   }
   __syncthreads();
   const int nkc = ni / 32;
@@ -400,8 +434,8 @@ struct SigSmem {
 };
 
 __global__ void __launch_bounds__(ST_THREADS, 1)
-    k_sig_tc(const __half* __restrict__ XS, const __half* __restrict__ WS, int ni, int npb, int ntau,
-             double* __restrict__ D, int np, int* __restrict__ err) {
+    k_sig_tc(const __half* __restrict__ XS, const float2* __restrict__ XE, const __half* __restrict__ WS, int ni,
+             int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const int BT = ni * 64;  // one W slice tile: ni rows x 64 B
@@ -477,12 +511,19 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
+    // Thread (quad, grp, lane) owns row 32 quad + lane and the 16-column blocks grp, grp + 4, ...
+    // Its XE values do not depend on tau: the first block's are fetched before the wait for
+    // the accumulators, each next block's while the current one is multiplied.
     const int quad = warp & 3, grp = warp >> 2;  // lane quadrant, column group
     const int row = 32 * quad + lane;
     const int p = pblk * 128 + row;
     const int nblk = ni / 16;  // 16-column blocks, dealt round-robin to the 4 column groups
     const double dscale = 1.0 / ((double)kScaleA * kScaleA * kScaleW);
+    const float2* xe = XE + ((size_t)k * npb + pblk) * ni * 128 + row;
     for (int it = 0; it < ntau; ++it) {
+      float2 xa[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) xa[c] = grp < nblk ? __ldg(xe + (size_t)(16 * grp + c) * 128) : make_float2(0.f, 0.f);
       const bool ok = wait_bar(&S.tfull, it & 1, &S.abort_flag, err);
       tc_fence_after();
       float dhi = 0.f, dlo = 0.f;  // compensated (two-sum) accumulator
@@ -492,27 +533,22 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
           float v1[16], v2[16];
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + n0, v1);
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + ni + n0, v2);
-          const int kc = n0 >> 5, col = n0 & 31;
+          float2 xb[16];
+          const bool more = bk + 4 < nblk;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) xb[c] = more ? __ldg(xe + (size_t)(n0 + 64 + c) * 128) : make_float2(0.f, 0.f);
           float part = 0.f;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const uint32_t off = sw64_off(row, col + 8 * h) / 2;
-            const h8 rh = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 0, npb, nkc) + off);
-            const h8 rl = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 1, npb, nkc) + off);
-            const h8 ih = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 2, npb, nkc) + off);
-            const h8 il = *reinterpret_cast<const h8*>(XS + xs_tile(k, pblk, kc, 3, npb, nkc) + off);
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const float xr = __half2float(rh.v[e]) + __half2float(rl.v[e]);
-              const float xi = __half2float(ih.v[e]) + __half2float(il.v[e]);
-              part = fmaf(xr, v1[8 * h + e], part);
-              part = fmaf(xi, v2[8 * h + e], part);
-            }
+          for (int c = 0; c < 16; ++c) {
+            part = fmaf(xa[c].x, v1[c], part);
+            part = fmaf(xa[c].y, v2[c], part);
           }
           const float s2 = dhi + part;
           const float bb = s2 - dhi;
           dlo += (dhi - (s2 - bb)) + (part - bb);
           dhi = s2;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) xa[c] = xb[c];
         }
       }
       tc_fence_before();
@@ -636,19 +672,21 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   const size_t xbytes = (size_t)4 * c->nk * npp * c->ni * sizeof(__half);
   const size_t wbytes = (size_t)4 * c->ntau * c->ni * c->ni * sizeof(__half);
   const size_t dbytes = (size_t)c->nk * np * c->ntau * sizeof(double);
+  const size_t ebytes = (size_t)c->nk * npp * c->ni * sizeof(float2);
   gw_status st;
-  if ((st = ensure(c, &c->mw.mslices, &c->mw.mslices_bytes, xbytes + wbytes + dbytes + 256, "Sigma slices")) !=
-      GW_OK)
+  if ((st = ensure(c, &c->mw.mslices, &c->mw.mslices_bytes, xbytes + wbytes + dbytes + ebytes + 256,
+                   "Sigma slices")) != GW_OK)
     return st;
   __half* XS = (__half*)c->mw.mslices;
   __half* WS = XS + xbytes / sizeof(__half);
   double* D = (double*)((char*)c->mw.mslices + xbytes + wbytes);
-  int* d_err = (int*)((char*)D + dbytes);
+  float2* XE = (float2*)((char*)D + dbytes);
+  int* d_err = (int*)((char*)XE + ebytes);
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
   if (c->mw.iq != iq || c->mw.prec != prec) {
     dim3 g(npp / 32, (c->ni + 31) / 32, c->nk);
-    k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->ni, np, npb, XS);
+    k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->ni, np, npb, XS, XE);
     if ((st = check_launch(c, "split_x")) != GW_OK) return st;
     c->mw.iq = iq;
     c->mw.prec = prec;
@@ -660,7 +698,7 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   const size_t smem = 1024 + 2 * stage_bytes + sizeof(SigSmem);
   cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(npb, c->nk);
-  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, WS, c->ni, npb, c->ntau, D, np, d_err);
+  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, npb, c->ntau, D, np, d_err);
   if ((st = check_launch(c, "sig_tc")) != GW_OK) return st;
   const int64_t n = (int64_t)c->nk * c->nb * c->ntau;
   k_sig_reduce<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(D, G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->nb,
