@@ -250,6 +250,14 @@ gw_status gw_copy_m(gw_ctx* ctx, int iq, int k0, int nk_copy, double* out);
 /* Number of kernels libgw has launched on this context since gw_create (host counter). */
 int64_t gw_launch_count(gw_ctx* ctx);
 
+/* Per-kernel device timing. gw_kernel_timing(ctx, 1) discards earlier records and from then on
+ * brackets every launch of the tensor-core contractions ("k_pol_tc", "k_sig_tc") and of the
+ * blocked screening ("k_screen_inv") with CUDA events on the context's stream; 0 stops.
+ * gw_kernel_time synchronises the stream and returns the summed device time (ms) and the
+ * number of recorded launches of the named kernel. No device memory is allocated. */
+gw_status gw_kernel_timing(gw_ctx* ctx, int enable);
+gw_status gw_kernel_time(gw_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
+
 /* Host-only (no GPU needed): the transform matrices gw_create builds for `grid`,
  * written to host arrays (NULL entries skipped):
  * B_fwd cplx [nnu][ntau], F_fwd cplx [nw][ntau], F_cont cplx [ncont][ntau],

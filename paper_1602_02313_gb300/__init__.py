@@ -33,6 +33,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
+           "gw_kernel_timing", "gw_kernel_time",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
            "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_get_params", "gw_mlp_set_params",
            "gw_cpe_features", "gw_cpe_fit_matrix", "gw_cpe_seed", "gw_cpe_iterations"]
@@ -109,6 +110,8 @@ def load_library(path=LIB_PATH):
         "gw_copy_m": [vp, i32, i32, i32, vp],
         "gw_transform_matrices": [ctypes.POINTER(_Grid), vp, vp, vp, vp, vp],
         "gw_launch_count": [vp],
+        "gw_kernel_timing": [vp, i32],
+        "gw_kernel_time": [vp, ctypes.c_char_p, vp, vp],
         "gw_screen_static": [i32, i32, i32, vp, vp, vp, vp, vp],
         "gw_mlp_create": [ctypes.POINTER(vp), i32, i32, i32, i32, ctypes.c_uint64, i32, vp],
         "gw_mlp_destroy": [vp], "gw_mlp_last_error": [vp], "gw_mlp_num_params": [vp],
@@ -203,6 +206,17 @@ class GW:
 
     def launch_count(self):
         return int(self.lib.gw_launch_count(self.h))
+
+    def kernel_timing(self, enable=True):
+        """Record CUDA events around the tensor-core and screening launches from now on."""
+        self._check(self.lib.gw_kernel_timing(self.h, int(bool(enable))), "gw_kernel_timing")
+
+    def kernel_time(self, name):
+        """(summed device ms, launches) of the named kernel since kernel_timing(True)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.lib.gw_kernel_time(self.h, name.encode(), ctypes.byref(ms), ctypes.byref(n)),
+                    "gw_kernel_time")
+        return float(ms.value), int(n.value)
 
     def sync(self):
         self._check(self.lib.gw_sync(self.h), "gw_sync")

@@ -18,6 +18,31 @@ gw_status set_err(gw_ctx* c, gw_status s, const std::string& msg) {
   return s;
 }
 
+void kt_begin(gw_ctx* c, const char* name) {
+  if (!c || !c->ktiming) return;
+  gw_ctx::KernelEvents e{name, nullptr, nullptr};
+  if (cudaEventCreate(&e.begin) != cudaSuccess || cudaEventCreate(&e.end) != cudaSuccess) {
+    cudaGetLastError();
+    if (e.begin) cudaEventDestroy(e.begin);
+    return;
+  }
+  cudaEventRecord(e.begin, c->stream);
+  c->kev.push_back(e);
+}
+
+void kt_end(gw_ctx* c) {
+  if (!c || !c->ktiming || c->kev.empty()) return;
+  cudaEventRecord(c->kev.back().end, c->stream);
+}
+
+static void kt_clear(gw_ctx* c) {
+  for (auto& e : c->kev) {
+    cudaEventDestroy(e.begin);
+    cudaEventDestroy(e.end);
+  }
+  c->kev.clear();
+}
+
 gw_status check_launch(gw_ctx* c, const char* what) {
   if (c) ++c->launches;
   cudaError_t e = cudaGetLastError();
@@ -493,6 +518,7 @@ gw_status gw_destroy(gw_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
+  kt_clear(c);
   double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
                     c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_b,
                     c->d_pade,  c->d_vm};
@@ -518,6 +544,30 @@ gw_status gw_sync(gw_ctx* c) {
 const char* gw_last_error(gw_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 int64_t gw_launch_count(gw_ctx* c) { return c ? c->launches : -1; }
+
+gw_status gw_kernel_timing(gw_ctx* c, int enable) {
+  if (!c) return GW_EINVAL;
+  kt_clear(c);
+  c->ktiming = enable != 0;
+  return GW_OK;
+}
+
+gw_status gw_kernel_time(gw_ctx* c, const char* kernel, double* total_ms, int64_t* launches) {
+  if (!c || !kernel || !total_ms || !launches) return GW_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, GW_ECUDA, "gw_kernel_time: stream");
+  double t = 0.0;
+  int64_t n = 0;
+  for (const auto& e : c->kev) {
+    if (std::strcmp(e.name, kernel) != 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.begin, e.end) != cudaSuccess) return set_err(c, GW_ECUDA, "gw_kernel_time: event");
+    t += ms;
+    ++n;
+  }
+  *total_ms = t;
+  *launches = n;
+  return GW_OK;
+}
 
 gw_status gw_green_tau(gw_ctx* c, const double* eps, const double* sigx, const double* vxc, const double* sigc_iw,
                        double* G, double* occ) {

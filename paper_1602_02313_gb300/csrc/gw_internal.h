@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 #else
 typedef struct CUstream_st* cudaStream_t;
+typedef struct CUevent_st* cudaEvent_t;
 #endif
 
 namespace gwi {
@@ -98,12 +99,22 @@ struct gw_ctx {
   size_t pade_bytes = 0;
   // tensor-core path
   gwi::MixedWork mw;
+  // per-kernel timing (gw_kernel_timing): CUDA events recorded around selected launches
+  struct KernelEvents {
+    const char* name;
+    cudaEvent_t begin, end;
+  };
+  bool ktiming = false;
+  std::vector<KernelEvents> kev;
   std::string err;
 };
 
 namespace gwi {
 // kernels and host launchers (defined in the .cu files)
 gw_status check_launch(gw_ctx* c, const char* what);
+// bracket a launch with CUDA events on the context's stream while timing is enabled
+void kt_begin(gw_ctx* c, const char* name);
+void kt_end(gw_ctx* c);
 gw_status set_err(gw_ctx* c, gw_status s, const std::string& msg);
 
 gw_status launch_gen_m(gw_ctx* c, double* M);

@@ -266,8 +266,10 @@ gw_status launch_inv(gw_ctx* c, int iq0, int nsys, const double* P, double* W, i
   using S = typename AR::S;
   const size_t smem = sizeof(S) * (GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1) + GJ_B * (GJ_B + 1));
   cudaFuncSetAttribute(k_screen_inv<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kt_begin(c, "k_screen_inv");
   k_screen_inv<AR><<<nsys, 256, smem, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu,
                                                    c->ni, reinterpret_cast<S*>(aug), (double2*)W, info);
+  kt_end(c);
   return check_launch(c, "screen");
 }
 

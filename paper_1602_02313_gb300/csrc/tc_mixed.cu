@@ -656,8 +656,10 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   if ((st = check_launch(c, "pol_weights")) != GW_OK) return st;
   const size_t smem = 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem);
   cudaFuncSetAttribute(k_pol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  kt_begin(c, "k_pol_tc");
   k_pol_tc<<<nunits, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips, d_strips, nseg,
                                                     d_part, d_err);
+  kt_end(c);
   if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
   const double scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
   k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
@@ -698,7 +700,9 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   const size_t smem = 1024 + 2 * stage_bytes + sizeof(SigSmem);
   cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(npb, c->nk);
+  kt_begin(c, "k_sig_tc");
   k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, npb, c->ntau, D, np, d_err);
+  kt_end(c);
   if ((st = check_launch(c, "sig_tc")) != GW_OK) return st;
   const int64_t n = (int64_t)c->nk * c->nb * c->ntau;
   k_sig_reduce<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(D, G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->nb,
