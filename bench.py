@@ -295,7 +295,10 @@ def main():
     tc = {k: v for k, v in kern.items() if k in ("k_pol_tc", "k_sig_tc")}
     if tc and prec != gw.GW_FP64:
         kname = max(tc, key=lambda k: tc[k]["total_ms"])
-        achieved = per_launch_flops[kname] / (tc[kname]["avg_ms"] * 1e-3) / 1e12
+        # one call per q and step (a call may hold several launches: P runs its K segments
+        # in passes when their partials exceed 8 GiB)
+        calls = len(chain.iqs) * args.steps
+        achieved = per_launch_flops[kname] * calls / (tc[kname]["total_ms"] * 1e-3) / 1e12
         label = kname + " (CUDA events around each launch)"
     else:
         dom = max(kt, key=lambda k: kt[k]) if kt else "selfenergy"

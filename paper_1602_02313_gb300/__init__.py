@@ -54,7 +54,7 @@ class _System(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("nk", ctypes.c_int), ("nq", ctypes.c_int), ("nb", ctypes.c_int),
                 ("nocc", ctypes.c_int), ("ni", ctypes.c_int), ("omega", ctypes.c_double),
                 ("kmq", ctypes.POINTER(ctypes.c_int)), ("v", ctypes.POINTER(ctypes.c_double)),
-                ("M", ctypes.c_void_p), ("q0", ctypes.c_int)]
+                ("M", ctypes.c_void_p), ("q0", ctypes.c_int), ("m_mode", ctypes.c_int)]
 
 
 def _grid_struct(grid, keep):
@@ -162,7 +162,7 @@ class GW:
     omega: unit-cell volume in 1/(Omega N_k).
     """
 
-    def __init__(self, grid, crystal, omega=1.0, device=0, stream=None, M=None, q0=0):
+    def __init__(self, grid, crystal, omega=1.0, device=0, stream=None, M=None, q0=0, m_mode=0):
         import torch
         self.lib = lib()
         self.device = device
@@ -177,7 +177,7 @@ class GW:
         g = _grid_struct(grid, self._h)
         s = _System(int(crystal.seed), crystal.nk, crystal.nq, crystal.nb, crystal.nocc, crystal.ni, self.omega,
                     self._h["kmq"].ctypes.data_as(ip), self._h["v"].ctypes.data_as(dp),
-                    None if M is None else ctypes.c_void_p(M.data_ptr()), int(q0))
+                    None if M is None else ctypes.c_void_p(M.data_ptr()), int(q0), int(m_mode))
         self._M = M
         h = ctypes.c_void_p()
         with torch.cuda.device(device):

@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(256) k_sigma_fp64(const double2* __restrict__ 
 gw_status launch_pol_fp64(gw_ctx* c, int iq, const double* G, double* P) {
   if (c->ni % PT) return set_err(c, GW_EUNSUPPORTED, "FP64 polarization needs ni % 32 == 0");
   const int nt = c->ni / PT;
-  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * c->nb * c->nb;
+  const double2* Mq = (const double2*)m_block(c, iq);
+  if (!Mq) return GW_ECUDA;
   dim3 grid(nt * (nt + 1) / 2, c->ntau);
   k_pol_fp64<<<grid, 256, 0, c->stream>>>(Mq, G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->ni, c->nb, c->ntau,
                                           1.0 / (c->omega * c->nk), (double2*)P);
@@ -185,7 +186,8 @@ gw_status launch_pol_fp64(gw_ctx* c, int iq, const double* G, double* P) {
 
 gw_status launch_sigma_fp64(gw_ctx* c, int iq, const double* G, const double* W, double* S) {
   if (c->ni % SJ) return set_err(c, GW_EUNSUPPORTED, "FP64 self-energy needs ni % 32 == 0");
-  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * c->nb * c->nb;
+  const double2* Mq = (const double2*)m_block(c, iq);
+  if (!Mq) return GW_ECUDA;
   dim3 grid((c->nb + SC - 1) / SC, c->ntau, c->nk);
   k_sigma_fp64<<<grid, 256, 0, c->stream>>>(Mq, G, (const double2*)W, c->d_kmq + (size_t)iq * c->nk, c->ni, c->nb,
                                             c->ntau, -1.0 / (c->omega * c->nk), S);

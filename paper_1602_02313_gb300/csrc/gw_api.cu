@@ -97,6 +97,21 @@ gw_status launch_gen_m(gw_ctx* c, double* M) {
   return check_launch(c, "gen_m");
 }
 
+const double* m_block(gw_ctx* c, int iq) {
+  const uint64_t per_q = (uint64_t)c->nk * c->ni * c->nb * c->nb;
+  if (!c->m_per_q) return c->d_M + 2 * (size_t)iq * per_q;
+  if (c->m_cur != iq) {
+    k_gen_m<<<152 * 8, 256, 0, c->stream>>>((double2*)c->d_M_own, per_q, (uint64_t)(c->q0 + iq) * per_q, c->seed,
+                                             std::sqrt(0.5 / c->nb));
+    if (check_launch(c, "gen_m") != GW_OK) {
+      c->m_cur = -1;
+      return nullptr;
+    }
+    c->m_cur = iq;
+  }
+  return c->d_M_own;
+}
+
 // ----------------------------------------------------------------------------
 // Reference Green's function G0_j(k|tau) = -exp(-eps tau)[1 - n_F(eps)] (Sec. III.B.1):
 // eps > 0: -exp(-eps tau)/(1 + exp(-beta eps)); eps <= 0: -exp(eps(beta - tau))/(1 + exp(beta eps)).
@@ -379,7 +394,8 @@ gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx) {
     }
     c->vm_bytes = need;
   }
-  const double2* M = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
+  const double2* M = (const double2*)m_block(c, iq);
+  if (!M) return GW_ECUDA;
   k_vm<<<dim3((np + 255) / 256, c->nk), 256, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->ni, np, c->d_vm);
   gw_status s = check_launch(c, "sigx_vm");
   if (s != GW_OK) return s;
@@ -493,14 +509,21 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
   if (s->M) {
     c->d_M = s->M;
   } else {
-    const size_t bytes = (size_t)c->nq * c->nk * c->ni * c->nb * c->nb * sizeof(double2);
-    if (cudaMalloc((void**)&c->d_M_own, bytes) != cudaSuccess) {
+    const size_t per_q = (size_t)c->nk * c->ni * c->nb * c->nb * sizeof(double2);
+    const size_t bytes = (size_t)c->nq * per_q;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    c->m_per_q = s->m_mode == 2 || (s->m_mode == 0 && bytes > free_b / 2);
+    if (cudaMalloc((void**)&c->d_M_own, c->m_per_q ? per_q : bytes) != cudaSuccess) {
       cudaGetLastError();
       gw_destroy(c);
       return GW_ENOMEM;
     }
     c->d_M = c->d_M_own;
-    if ((st = launch_gen_m(c, c->d_M_own)) != GW_OK) {
+    if (!c->m_per_q && (st = launch_gen_m(c, c->d_M_own)) != GW_OK) {
       gw_destroy(c);
       return st;
     }
@@ -637,7 +660,9 @@ gw_status gw_continue(gw_ctx* c, gw_cont_method method, int64_t nprob, const dou
 gw_status gw_copy_m(gw_ctx* c, int iq, int k0, int nkc, double* out) {
   if (!c || !out || iq < 0 || iq >= c->nq || k0 < 0 || nkc < 1 || k0 + nkc > c->nk) return GW_EINVAL;
   const size_t per_k = (size_t)c->ni * c->nb * c->nb * sizeof(double2);
-  const char* src = (const char*)c->d_M + ((size_t)iq * c->nk + k0) * per_k;
+  const double* mq = m_block(c, iq);
+  if (!mq) return GW_ECUDA;
+  const char* src = (const char*)mq + (size_t)k0 * per_k;
   if (cudaMemcpyAsync(out, src, per_k * nkc, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
     return set_err(c, GW_ECUDA, "gw_copy_m");
   return GW_OK;

@@ -66,8 +66,10 @@ struct gw_ctx {
   double* d_tau = nullptr;     // [ntau]
   double* d_sqrtv = nullptr;   // [nq][ni]
   double* d_v = nullptr;       // [nq][ni]
-  const double* d_M = nullptr; // cplx [nq][nk][ni][nb][nb]
+  const double* d_M = nullptr; // cplx [nq][nk][ni][nb][nb], or one q's block when m_per_q
   double* d_M_own = nullptr;
+  bool m_per_q = false;        // M generated one q at a time into d_M_own
+  int m_cur = -1;              // the q whose block d_M_own holds (m_per_q)
   double* d_Bfwd = nullptr;    // cplx [nnu][ntau]
   double* d_Ffwd = nullptr;    // cplx [nw][ntau]
   double* d_Fcont = nullptr;   // cplx [ncont][ntau]
@@ -118,6 +120,9 @@ void kt_end(gw_ctx* c);
 gw_status set_err(gw_ctx* c, gw_status s, const std::string& msg);
 
 gw_status launch_gen_m(gw_ctx* c, double* M);
+// device address of M[iq] ([nk][ni][nb][nb] cplx); with per-q generation, (re)generates the
+// block first when it holds another q. NULL on a launch error (set in the context).
+const double* m_block(gw_ctx* c, int iq);
 gw_status launch_green0(gw_ctx* c, const double* eps, double* G, double* occ);
 gw_status launch_dyson(gw_ctx* c, const double* eps, const double* sigx, const double* vxc,
                        const double* sigc_iw, double* G, double* occ);

@@ -111,12 +111,14 @@ __global__ void __launch_bounds__(512) k_screen(const double2* __restrict__ P, c
 // formed (ni^3 complex multiply-adds instead of the 1.5 ni^3 of eliminating [A | Pi]).
 // For each 32-row block R: invert the pivot block A_RR in shared memory (no pivoting),
 // U_c = A_RR^-1 A_Rc for every column block c != R, A_ic -= A_iR U_c for every row i
-// outside R, A_iR <- -A_iR A_RR^-1 and A_RR <- A_RR^-1. The rank-32 updates are
-// register-tiled (8 rows x 4 columns per thread) from shared memory, so the matrix is
-// read and written once per block row.
+// outside R, A_iR <- -A_iR A_RR^-1 and A_RR <- A_RR^-1. The new rows R are written first;
+// the other rows follow in passes of 256, each pass holding its 32-column panel A_iR in
+// shared memory. The rank-32 updates are register-tiled (8 rows x 4 columns per thread), so
+// the matrix is read and written once per block row, for any ni that is a multiple of 32.
 //
 // The arithmetic is a policy (arith.cuh): native FP64, or float-float on the FP32 pipes.
 constexpr int GJ_B = 32;
+constexpr int GJ_RP = 256;  // rows per update pass (the shared-memory panel)
 
 using arith::Fp64;
 using arith::Ff32;
@@ -129,8 +131,8 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
   using Acc = typename AR::Acc;
   extern __shared__ __align__(16) unsigned char gsm_raw[];
   S* Pinv = reinterpret_cast<S*>(gsm_raw);  // [32][33]
-  S* L = Pinv + GJ_B * (GJ_B + 1);           // [ni][33]: A[i][R] for all rows (rows of R zeroed)
-  S* U = L + (size_t)ni * (GJ_B + 1);        // [32][33]
+  S* L = Pinv + GJ_B * (GJ_B + 1);           // [GJ_RP][33]: A[i][R] of one row pass (rows of R zeroed)
+  S* U = L + (size_t)GJ_RP * (GJ_B + 1);     // [32][33]
   __shared__ int bad;
   __shared__ S fcol[GJ_B], rowj[GJ_B];
   const int sys = blockIdx.x;
@@ -152,10 +154,6 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
     for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
       const int r = e / GJ_B, c = e % GJ_B;
       Pinv[r * (GJ_B + 1) + c] = A[(size_t)(k0 + r) * ni + k0 + c];
-    }
-    for (int e = t; e < ni * GJ_B; e += blockDim.x) {
-      const int r = e / GJ_B, c = e % GJ_B;
-      L[r * (GJ_B + 1) + c] = (r >= k0 && r < k0 + GJ_B) ? AR::zero() : A[(size_t)r * ni + k0 + c];
     }
     __syncthreads();
     // in-place Gauss-Jordan inversion of the 32 x 32 pivot block (no pivoting):
@@ -192,9 +190,9 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
     }
     __syncthreads();
     if (bad) break;
+    // rows R: A_Rc <- A_RR^-1 A_Rc for every column block c != R, A_RR <- A_RR^-1
     for (int c0 = 0; c0 < ni; c0 += GJ_B) {
       const bool isR = c0 == k0;
-      // U = A_RR^-1 A_R,chunk (the pivot block inverse itself for the chunk R)
       for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
         const int r = e / GJ_B, c = e % GJ_B;
         S u;
@@ -212,9 +210,24 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
         const int r = e / GJ_B, c = e % GJ_B;
         A[(size_t)(k0 + r) * ni + c0 + c] = U[r * (GJ_B + 1) + c];
       }
-      // rank-32 update of all rows outside R: thread (tr, tc) owns rows tr + 32 m, columns 4 tc .. 4 tc + 3;
-      // the chunk R starts from zero (A_iR <- -A_iR A_RR^-1)
-      for (int rbase = 0; rbase < ni; rbase += 256) {
+      __syncthreads();
+    }
+    // all other rows, in passes of GJ_RP rows: A_ic -= A_iR U_c with U_c the new row block
+    // (A_iR <- -A_iR A_RR^-1 for the column block R, which starts from zero); the pass's
+    // A_iR are taken into shared memory before its column block R is overwritten
+    for (int r0 = 0; r0 < ni; r0 += GJ_RP) {
+      for (int e = t; e < GJ_RP * GJ_B; e += blockDim.x) {
+        const int r = e / GJ_B, c = e % GJ_B, gr = r0 + r;
+        L[r * (GJ_B + 1) + c] = (gr >= ni || (gr >= k0 && gr < k0 + GJ_B)) ? AR::zero() : A[(size_t)gr * ni + k0 + c];
+      }
+      for (int c0 = 0; c0 < ni; c0 += GJ_B) {
+        const bool isR = c0 == k0;
+        for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
+          const int r = e / GJ_B, c = e % GJ_B;
+          U[r * (GJ_B + 1) + c] = A[(size_t)(k0 + r) * ni + c0 + c];
+        }
+        __syncthreads();
+        // thread (tr, tc) owns rows r0 + tr + 32 m and columns 4 tc .. 4 tc + 3 of the chunk
         Acc acc[8][4];
 #pragma unroll
         for (int m = 0; m < 8; ++m)
@@ -226,15 +239,14 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
           for (int q = 0; q < 4; ++q) uq[q] = U[j * (GJ_B + 1) + 4 * tc + q];
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
-            const int r = rbase + tr + 32 * m;
-            const S l = r < ni ? L[r * (GJ_B + 1) + j] : AR::zero();
+            const S l = L[(tr + 32 * m) * (GJ_B + 1) + j];
 #pragma unroll
             for (int q = 0; q < 4; ++q) AR::mac(acc[m][q], l, uq[q]);
           }
         }
 #pragma unroll
         for (int m = 0; m < 8; ++m) {
-          const int r = rbase + tr + 32 * m;
+          const int r = r0 + tr + 32 * m;
           if (r >= ni || (r >= k0 && r < k0 + GJ_B)) continue;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -242,8 +254,8 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
             *a = AR::sub(isR ? AR::zero() : *a, acc[m][q]);
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
     }
   }
   if (bad) {
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
 template <class AR>
 gw_status launch_inv(gw_ctx* c, int iq0, int nsys, const double* P, double* W, int* info, double* aug) {
   using S = typename AR::S;
-  const size_t smem = sizeof(S) * (GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1) + GJ_B * (GJ_B + 1));
+  const size_t smem = sizeof(S) * (2 * GJ_B * (GJ_B + 1) + (size_t)GJ_RP * (GJ_B + 1));
   cudaFuncSetAttribute(k_screen_inv<AR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kt_begin(c, "k_screen_inv");
   k_screen_inv<AR><<<nsys, 256, smem, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu,
@@ -277,10 +289,9 @@ gw_status launch_inv(gw_ctx* c, int iq0, int nsys, const double* P, double* W, i
 
 gw_status launch_screen(gw_ctx* c, int iq0, int nqb, int prec, const double* P, double* W, int* info, double* aug) {
   const int nsys = nqb * c->nnu;
-  const size_t smem = sizeof(double2) * (2 * GJ_B * (GJ_B + 1) + (size_t)c->ni * (GJ_B + 1));
-  const bool blocked = c->ni % GJ_B == 0 && smem <= 200 * 1024;
+  const bool blocked = c->ni % GJ_B == 0;
   if (prec == GW_F32X2) {
-    if (!blocked) return set_err(c, GW_EUNSUPPORTED, "gw_screen: GW_F32X2 needs ni a multiple of 32 and ni <= 320");
+    if (!blocked) return set_err(c, GW_EUNSUPPORTED, "gw_screen: GW_F32X2 needs ni a multiple of 32");
     return launch_inv<Ff32>(c, iq0, nsys, P, W, info, aug);
   }
   if (prec != GW_FP64) return set_err(c, GW_EUNSUPPORTED, "gw_screen: precision must be GW_FP64 or GW_F32X2");

@@ -73,6 +73,7 @@ struct alignas(16) h8 {
 // slices hi, lo. The scaled operand X = w_tau(p) A (rows of the strip) is built by the
 // producer warps from the same image. TMEM holds Re P (N columns) and Im P (N columns).
 constexpr int kPolChunksPerSeg = 32;
+constexpr size_t kPolPartBytes = 8ull << 30;  // at most 8 GiB of FP32 partial strips at once
 constexpr int PT_THREADS = 288;                     // warps 0-7 produce / run the epilogue, warp 8 issues MMAs
 constexpr int P_XT = 16384;                         // one X slice: 128 rows x 128 B
 constexpr int P_STAGE_BYTES = 2 * P_XT + 2 * 256 * 128;  // X hi, lo (128 rows) + Y hi, lo (<= 256 rows)
@@ -132,14 +133,14 @@ __global__ void k_split_y(const double2* __restrict__ Mq, int nk, int ni, int np
 
 __global__ void __launch_bounds__(PT_THREADS, 1)
     k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
-             int npw, int nstrips, const int4* __restrict__ strips, int nseg, float* __restrict__ part,
+             int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, float* __restrict__ part,
              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int u = blockIdx.x;
-  const int it = u % ntau, strip = (u / ntau) % nstrips, seg = u / (ntau * nstrips);
+  const int it = u % ntau, strip = (u / ntau) % nstrips, seg = seg0 + u / (ntau * nstrips);
   const int4 sd = strips[strip];                 // (row block, c0, N, -)
   const int xb = sd.x, c0 = sd.y, N = sd.z;
   const int nib = (ni + 127) / 128;
@@ -309,7 +310,7 @@ __device__ __forceinline__ void two_sum_acc(float& h, float& l, float x) {
 __global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ part, int ni, int ntau,
                                                     const int* __restrict__ strip_of, int nstrips,
                                                     const int4* __restrict__ strips, int nseg, double scale,
-                                                    double2* __restrict__ P) {
+                                                    int accumulate, double2* __restrict__ P) {
   __shared__ double2 tr[32][33];
   const int nb32 = (ni + 31) / 32;
   int t = blockIdx.x, ab = 0;
@@ -346,6 +347,11 @@ __global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ pa
     const int a = ab * 32 + ty + 8 * r;
     double2 v = make_double2(((double)reh[r] + (double)rel[r]) * scale, ((double)imh[r] + (double)iml[r]) * scale);
     if (a == b) v.y = 0.0;  // Im P_II = 0 exactly (the tensor-core sum leaves O(2^-22) residue)
+    if (accumulate && a < ni && b < ni) {  // a later pass over K segments: add to the earlier sum
+      const double2 o = Pt[(size_t)a * ni + b];
+      v.x += o.x;
+      v.y += o.y;
+    }
     if (a < ni && b < ni && (ab < bb || a <= b)) Pt[(size_t)a * ni + b] = v;
     tr[ty + 8 * r][tx] = make_double2(v.x, -v.y);
   }
@@ -433,19 +439,24 @@ struct SigSmem {
   float red[4][128];
 };
 
+// The NI output columns are processed in nh parts of NC = NI / nh <= 256 columns (TMEM holds Y1
+// and Y2 of one part: 2 NC <= 512 columns). Work units u = (tau, part), each a run of NI / 32
+// K chunks; the epilogue sums d_p over the parts of a tau before writing it.
 __global__ void __launch_bounds__(ST_THREADS, 1)
     k_sig_tc(const __half* __restrict__ XS, const float2* __restrict__ XE, const __half* __restrict__ WS, int ni,
-             int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err) {
+             int nh, int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  const int BT = ni * 64;  // one W slice tile: ni rows x 64 B
+  const int NC = ni / nh;  // output columns per part
+  const int BT = NC * 64;  // one W slice tile of a part: NC rows x 64 B
   const int a_bytes = 4 * S_ATILE, b_bytes = 4 * BT;
   const int stage_bytes = a_bytes + b_bytes;
   SigSmem& S = *reinterpret_cast<SigSmem*>(base + 2 * stage_bytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int pblk = blockIdx.x, k = blockIdx.y;
   const int nkc = ni / 32;
-  const int nchunk = ntau * nkc;
+  const int nunit = ntau * nh;
+  const int nchunk = nunit * nkc;
   const int PW = ST_EPI_WARPS, MW = ST_EPI_WARPS + 1;
 
   if (tid == 0) {
@@ -465,26 +476,32 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
   const uint32_t tbase = S.tslot;
 
   if (warp == PW) {
-    // ------------------------------------------------------------ producer: two bulk copies per chunk
+    // ------------------------------------------------------------ producer: bulk copies per chunk
     if (lane == 0) {
       for (int i = 0; i < nchunk; ++i) {
         const int s = i & 1;
         if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
-        const int it = i / nkc, kc = i % nkc;
+        const int u = i / nkc, kc = i % nkc, it = u / nh, h = u % nh;
         unsigned char* st = base + s * stage_bytes;
         mbar_arrive_expect_tx(&S.full[s], (uint32_t)stage_bytes);
         bulk_g2s(st, XS + xs_tile(k, pblk, kc, 0, npb, nkc), (uint32_t)a_bytes, &S.full[s]);
-        bulk_g2s(st + a_bytes, WS + ((size_t)it * nkc + kc) * 4 * ((size_t)ni * 32), (uint32_t)b_bytes, &S.full[s]);
+        const __half* w0 = WS + ((size_t)it * nkc + kc) * 4 * ((size_t)ni * 32);
+        if (nh == 1) {
+          bulk_g2s(st + a_bytes, w0, (uint32_t)b_bytes, &S.full[s]);
+        } else {
+          for (int sl = 0; sl < 4; ++sl)
+            bulk_g2s(st + a_bytes + sl * BT, w0 + (size_t)sl * ni * 32 + (size_t)h * NC * 32, (uint32_t)BT, &S.full[s]);
+        }
       }
     }
   } else if (warp == MW) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id = idesc_f16(128, ni, false, false);
-      const uint32_t y1 = tbase, y2 = tbase + ni;
+      const uint32_t id = idesc_f16(128, NC, false, false);
+      const uint32_t y1 = tbase, y2 = tbase + NC;
       for (int i = 0; i < nchunk; ++i) {
-        const int s = i & 1, it = i / nkc, kc = i % nkc;
-        if (kc == 0 && it > 0 && !wait_bar(&S.tempty, (it - 1) & 1, &S.abort_flag, err)) break;
+        const int s = i & 1, u = i / nkc, kc = i % nkc;
+        if (kc == 0 && u > 0 && !wait_bar(&S.tempty, (u - 1) & 1, &S.abort_flag, err)) break;
         if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) break;
         tc_fence_after();
         const uint32_t st = smem_u32(base + s * stage_bytes);
@@ -512,31 +529,34 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
   } else {
     // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
     // Thread (quad, grp, lane) owns row 32 quad + lane and the 16-column blocks grp, grp + 4, ...
-    // Its XE values do not depend on tau: the first block's are fetched before the wait for
-    // the accumulators, each next block's while the current one is multiplied.
+    // of each part. Its XE values do not depend on tau: a part's first block is fetched before
+    // the wait for the accumulators, each next block while the current one is multiplied.
     const int quad = warp & 3, grp = warp >> 2;  // lane quadrant, column group
     const int row = 32 * quad + lane;
     const int p = pblk * 128 + row;
-    const int nblk = ni / 16;  // 16-column blocks, dealt round-robin to the 4 column groups
+    const int nblk = NC / 16;  // 16-column blocks of a part, dealt round-robin to the 4 column groups
     const double dscale = 1.0 / ((double)kScaleA * kScaleA * kScaleW);
     const float2* xe = XE + ((size_t)k * npb + pblk) * ni * 128 + row;
-    for (int it = 0; it < ntau; ++it) {
+    float dhi = 0.f, dlo = 0.f;  // compensated (two-sum) accumulator over the parts of one tau
+    for (int u = 0; u < nunit; ++u) {
+      const int it = u / nh, h = u % nh;
+      const float2* xh = xe + (size_t)h * NC * 128;
+      if (h == 0) dhi = dlo = 0.f;
       float2 xa[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) xa[c] = grp < nblk ? __ldg(xe + (size_t)(16 * grp + c) * 128) : make_float2(0.f, 0.f);
-      const bool ok = wait_bar(&S.tfull, it & 1, &S.abort_flag, err);
+      for (int c = 0; c < 16; ++c) xa[c] = grp < nblk ? __ldg(xh + (size_t)(16 * grp + c) * 128) : make_float2(0.f, 0.f);
+      const bool ok = wait_bar(&S.tfull, u & 1, &S.abort_flag, err);
       tc_fence_after();
-      float dhi = 0.f, dlo = 0.f;  // compensated (two-sum) accumulator
       if (ok) {
         for (int bk = grp; bk < nblk; bk += 4) {
           const int n0 = 16 * bk;
           float v1[16], v2[16];
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + n0, v1);
-          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + ni + n0, v2);
+          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + NC + n0, v2);
           float2 xb[16];
           const bool more = bk + 4 < nblk;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) xb[c] = more ? __ldg(xe + (size_t)(n0 + 64 + c) * 128) : make_float2(0.f, 0.f);
+          for (int c = 0; c < 16; ++c) xb[c] = more ? __ldg(xh + (size_t)(n0 + 64 + c) * 128) : make_float2(0.f, 0.f);
           float part = 0.f;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -553,6 +573,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
       }
       tc_fence_before();
       mbar_arrive(&S.tempty);
+      if (h != nh - 1) continue;
       // combine the four column groups of each row
       S.red[grp][row] = dhi + dlo;  // dlo is the two-sum error term of dhi
       asm volatile("bar.sync 1, %0;" ::"r"(ST_EPI_WARPS * 32) : "memory");
@@ -627,8 +648,11 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   const int base_units = nstrips * c->ntau;
   int nseg = std::max(1, (total + kPolChunksPerSeg - 1) / kPolChunksPerSeg);
   while (base_units * nseg < 2 * sms && (total + nseg) / (nseg + 1) >= 4) ++nseg;
-  const int nunits = base_units * nseg;
-  const size_t part_bytes = (size_t)nunits * 2 * 128 * 256 * sizeof(float);
+  // the partials of at most kPolPartBytes are held at once: segments run in passes, each
+  // reduced into P (the first pass writes, later ones add)
+  const size_t seg_bytes = (size_t)base_units * 2 * 128 * 256 * sizeof(float);
+  const int seg_pass = (int)std::max<size_t>(1, std::min<size_t>(nseg, kPolPartBytes / seg_bytes));
+  const size_t part_bytes = seg_bytes * seg_pass;
   const size_t wt_bytes = (size_t)c->nk * c->ntau * npw * sizeof(float);
   const size_t ys_bytes = (size_t)c->nk * cpk * nib * 2 * 128 * 64 * sizeof(__half);
   gw_status st;
@@ -646,7 +670,8 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   cudaMemcpyAsync(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice, c->stream);
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   if (ni % 128) cudaMemsetAsync(d_ys, 0, ys_bytes, c->stream);  // rows >= ni of the last block stay zero
-  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * ni * np;
+  const double2* Mq = (const double2*)m_block(c, iq);
+  if (!Mq) return GW_ECUDA;
   const int64_t nsp = (int64_t)c->nk * ni * cpk * 4;
   k_split_y<<<(unsigned)((nsp + 255) / 256), 256, 0, c->stream>>>(Mq, c->nk, ni, np, cpk, nib, d_ys);
   if ((st = check_launch(c, "split_y")) != GW_OK) return st;
@@ -656,20 +681,27 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   if ((st = check_launch(c, "pol_weights")) != GW_OK) return st;
   const size_t smem = 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem);
   cudaFuncSetAttribute(k_pol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kt_begin(c, "k_pol_tc");
-  k_pol_tc<<<nunits, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips, d_strips, nseg,
-                                                    d_part, d_err);
-  kt_end(c);
-  if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
   const double scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
-  k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
-                                                                           d_strips, nseg, scale, (double2*)P);
-  return check_launch(c, "pol_reduce");
+  for (int s0 = 0; s0 < nseg; s0 += seg_pass) {
+    const int ns = std::min(seg_pass, nseg - s0);
+    kt_begin(c, "k_pol_tc");
+    k_pol_tc<<<base_units * ns, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips,
+                                                               d_strips, nseg, s0, d_part, d_err);
+    kt_end(c);
+    if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
+    k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
+                                                                             d_strips, ns, scale, s0 > 0 ? 1 : 0,
+                                                                             (double2*)P);
+    if ((st = check_launch(c, "pol_reduce")) != GW_OK) return st;
+  }
+  return GW_OK;
 }
 
 gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W, int prec, double* S) {
   if (prec != GW_FP16X2) return set_err(c, GW_EUNSUPPORTED, "self-energy: only GW_FP16X2 is built on tensor cores");
-  if (c->ni > 256) return set_err(c, GW_EUNSUPPORTED, "tensor-core self-energy: ni <= 256");
+  const int nh = (c->ni + 255) / 256;  // output-column parts of <= 256 columns
+  if (c->ni % 32 || c->ni % (16 * nh))
+    return set_err(c, GW_EUNSUPPORTED, "tensor-core self-energy: ni a multiple of 32 that splits into parts of 16k columns");
   const int np = c->nb * c->nb, npb = (np + 127) / 128, npp = npb * 128;
   const size_t xbytes = (size_t)4 * c->nk * npp * c->ni * sizeof(__half);
   const size_t wbytes = (size_t)4 * c->ntau * c->ni * c->ni * sizeof(__half);
@@ -685,8 +717,9 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   float2* XE = (float2*)((char*)D + dbytes);
   int* d_err = (int*)((char*)XE + ebytes);
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
-  const double2* Mq = (const double2*)c->d_M + (size_t)iq * c->nk * c->ni * np;
   if (c->mw.iq != iq || c->mw.prec != prec) {
+    const double2* Mq = (const double2*)m_block(c, iq);
+    if (!Mq) return GW_ECUDA;
     dim3 g(npp / 32, (c->ni + 31) / 32, c->nk);
     k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->ni, np, npb, XS, XE);
     if ((st = check_launch(c, "split_x")) != GW_OK) return st;
@@ -696,12 +729,12 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   const int64_t nw = (int64_t)c->ntau * c->ni * c->ni;
   k_split_w<<<(unsigned)((nw + 255) / 256), 256, 0, c->stream>>>((const double2*)W, c->ntau, c->ni, WS);
   if ((st = check_launch(c, "split_w")) != GW_OK) return st;
-  const int stage_bytes = 4 * S_ATILE + 4 * c->ni * 64;
+  const int stage_bytes = 4 * S_ATILE + 4 * (c->ni / nh) * 64;
   const size_t smem = 1024 + 2 * stage_bytes + sizeof(SigSmem);
   cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(npb, c->nk);
   kt_begin(c, "k_sig_tc");
-  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, npb, c->ntau, D, np, d_err);
+  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, nh, npb, c->ntau, D, np, d_err);
   kt_end(c);
   if ((st = check_launch(c, "sig_tc")) != GW_OK) return st;
   const int64_t n = (int64_t)c->nk * c->nb * c->ntau;

@@ -48,7 +48,7 @@ class Chain:
         # the dielectric solve and the bosonic transforms: native FP64 on the FP64 chain,
         # float-float on the mixed one
         if screen_prec is None:
-            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 or ctx.cr.ni > 320 else GW_F32X2
+            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32X2
         self.screen_prec = screen_prec
         self.iqs = list(range(cr.nq)) if iqs is None else list(iqs)
         self.qb = max(1, min(qb, len(self.iqs)))

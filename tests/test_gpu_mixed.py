@@ -147,3 +147,43 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
         assert eS < 1e-3
     a, b = res[("fp64", gw.GW_CPE)], res[("fp16x2", gw.GW_CPE)]
     assert abs(gap(a["eqp"]) - gap(b["eqp"])) * ha2mev < 1.0  # the 1 meV target, CPE continuation
+
+
+def test_ni512_shapes_tc_vs_fp64(gw):
+    """The Nk=216 crystal's band and basis sizes (Nb = 128, NI = 512, Ntau = 64, beta = 400) at
+    Nk = 8, one q: tensor-core P (K segments in two passes over the partial buffer) and Sigma
+    (output columns in two parts of 256) against the FP64 GPU path; M generated per q on demand
+    must equal M generated at context creation."""
+    import torch
+    cr, gr = gi.make_config("nk216_nb128", nk=8, qlist=[3])
+    ctx = gw.GW(gr, cr, m_mode=2)
+    ref = gw.GW(gr, cr, m_mode=1)
+    a = torch.empty((2, cr.ni, cr.nb, cr.nb), dtype=torch.complex128, device="cuda")
+    b = torch.empty_like(a)
+    ctx.copy_m(0, 5, 2, a)
+    ref.copy_m(0, 5, 2, b)
+    ctx.sync()
+    ref.sync()
+    assert torch.equal(a, b)
+    ref.close()
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    Gd = dev(G)
+    P64 = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    P16 = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+    ctx.polarization(0, Gd, P64, gw.GW_FP64)
+    ctx.polarization(0, Gd, P16, gw.GW_FP16X2)
+    ctx.sync()
+    e = rel(host(P16), host(P64))
+    print(f"NI=512: P tensor-core vs FP64 rel err {e:.3e}")
+    assert e < TOL_P
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((gr.ntau, cr.ni, 16)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 16))
+    W = dev(-(X @ np.conj(np.swapaxes(X, 1, 2))) * 5.0)
+    S64 = zeros((cr.nk, cr.nb, gr.ntau))
+    S16 = zeros((cr.nk, cr.nb, gr.ntau))
+    ctx.selfenergy(0, Gd, dev(occ), W, S64, None, gw.GW_FP64)
+    ctx.selfenergy(0, Gd, dev(occ), W, S16, None, gw.GW_FP16X2)
+    ctx.sync()
+    e = rel(host(S16), host(S64))
+    print(f"NI=512: Sigma tensor-core vs FP64 rel err {e:.3e}")
+    assert e < TOL_S

@@ -178,10 +178,11 @@ def _screen_systems(ni, nnu, seed):
     return P, v
 
 
-@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
-def test_screen_full_size(gw, prec):
-    """One q point's 48 systems at NI = 256 (the benchmarked crystal's size), both arithmetics."""
-    cr, gr = gi.make_config("nk64_nb64", qlist=[0], nk=8)
+@pytest.mark.parametrize("prec,ni", [("fp64", 256), ("f32x2", 256), ("fp64", 512), ("f32x2", 512)])
+def test_screen_full_size(gw, prec, ni):
+    """One q point's 48 systems at NI = 256 (the benchmarked crystal's size) and NI = 512 (two
+    row passes of the blocked inverse), both arithmetics."""
+    cr, gr = gi.make_config("nk64_nb64", qlist=[0], nk=8, ni=ni, nb=16, nocc=8)
     P, v = _screen_systems(cr.ni, gr.nnu, 77)
     cr.v[0] = v
     ctx = gw.GW(gr, cr, omega=0.7)
@@ -192,7 +193,7 @@ def test_screen_full_size(gw, prec):
     assert np.all(host(info) == 0)
     ref = orc.screen(P, v)
     err = rel(host(W)[0], ref)
-    print(f"screen NI=256 {prec}: rel err {err:.2e}")
+    print(f"screen NI={ni} {prec}: rel err {err:.2e}")
     assert err < (TOL if prec == "fp64" else TOL_F32X2)
 
 
