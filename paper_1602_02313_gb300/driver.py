@@ -38,7 +38,7 @@ def contraction_flops(nk, nb, ni, ntau):
 class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
-    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-5, mlp=None,
+    def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-3, mlp=None,
                  nfit=64, screen_prec=None):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
@@ -76,6 +76,8 @@ class Chain:
         self.timers = None
         self.mlp = mlp
         if cont_method == GW_CPE:
+            # ridge 1e-3 (relative to ||A||_F): above the noise of the mixed chain's Sigma(i w), so
+            # that the fit, and the QP root it leads to, do not jump with rounding-level changes
             self.cpe_x = cpe_grid()
             ctx.cpe_setup(self.cpe_x, cpe_ridge)
         if mlp is not None:
