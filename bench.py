@@ -287,9 +287,13 @@ def main():
             kern[name] = {"launches": n, "total_ms": tot, "avg_ms": tot / n}
     ctx.kernel_timing(False)
     per_launch_flops = {"polarization": fp, "selfenergy": fs, "k_pol_tc": fp, "k_sig_tc": fs}
-    # tensor-core MMA flops per algorithmic flop: 3 split products; P's 128-row strips cover
-    # 1.5x the Hermitian half at NI = 256; Sigma's 3 NI^2 real GEMM per pair vs 4 NI^2 counted
-    mma_factor = {"k_pol_tc": 3.0 * 1.5, "k_sig_tc": 3.0 * 3.0 / 4.0}
+    # tensor-core MMA flops per algorithmic flop: 3 split products; P's 128-row strips cover the
+    # Hermitian half (NI^2 / 2) with sum_i 128 (NI - 128 i) outputs; Sigma runs 4 real GEMMs over
+    # the upper triangle of W~, (nkc + 1) / (2 nkc) of the columns, against 4 NI^2 MACs counted
+    ni_ = cr.ni
+    strip_cover = sum(128 * (ni_ - 128 * i) for i in range((ni_ + 127) // 128)) / (ni_ * ni_ / 2.0)
+    nkc_ = ni_ // 32
+    mma_factor = {"k_pol_tc": 3.0 * strip_cover, "k_sig_tc": 3.0 * (nkc_ + 1) / (2.0 * nkc_)}
     peaks = _peaks()
     peak = peaks["tensor_sustained"]
     tc = {k: v for k, v in kern.items() if k in ("k_pol_tc", "k_sig_tc")}

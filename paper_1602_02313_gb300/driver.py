@@ -145,6 +145,18 @@ class Chain:
         self.start_g0()
         self.sigma()
         self.finish()
+        self.vxc = self.Sx.clone()  # Sigma_0 = Sigma^x[G0], kept fixed by the later passes
+
+    def iterate(self, n):
+        """n self-consistent passes after step(): P, W~ and Sigma from the previous pass's
+        dressed G (Eqs. dysongf-zcjk solved in i w), the Dyson update from the band energies
+        with the new Sigma and the fixed reference potential."""
+        if self.vxc is None:
+            raise GwError("Chain.iterate: run step() first")
+        for _ in range(n):
+            G, occ = self.G1.clone(), self.occ1.clone()
+            self.sigma(G, occ)
+            self.finish(self.vxc)
 
     def check(self):
         ctx = self.ctx

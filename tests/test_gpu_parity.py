@@ -350,6 +350,30 @@ def test_g0w0_chain_small(gw, small):
     assert np.abs(host(occ1) - occ1r).max() < TOL
 
 
+def test_scgw_two_passes_small(gw, small):
+    """G0W0 then one self-consistent pass (P, W~, Sigma from the dressed G), FP64 chain on the GPU
+    against the oracle repeating its chain with the dressed G."""
+    from paper_1602_02313_gb300.driver import Chain
+    cr, gr, ctx = small
+    ch = Chain(ctx, dev(cr.eps), prec=gw.GW_FP64, qb=1, cont_method=gw.GW_PADE)
+    ch.step()
+    ch.iterate(1)
+    ch.check()
+    M = gi.m_for_q(cr, 0)
+    G, f = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    vxc = None
+    for _ in range(2):
+        Wt = orc.nu_to_tau(orc.screen(orc.tau_to_nu(orc.polarization(M, G, cr.kmq[0]), gr), cr.v[0]), gr)
+        S, Sx, _ = orc.selfenergy(M, G, Wt, cr.v[0], cr.kmq[0], f)
+        if vxc is None:
+            vxc = Sx
+        G, f = orc.dyson_iw(cr.eps, Sx, vxc, orc.sigma_tau_to_iw(S, gr), gr)
+    assert rel(host(ch.S), S) < TOL
+    assert rel(host(ch.Sx), Sx) < TOL
+    assert rel(host(ch.G1), G) < TOL
+    assert rel(host(ch.occ1), f) < TOL  # -G(beta^-) of the dressed G: O(1) to O(10) here
+
+
 # ------------------------------------------------------------------ full size (Nk=64, Nb=64, NI=256), sampled
 def test_c2_full_size_sampled(gw):
     """The bench workload's sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): FP64 P of
