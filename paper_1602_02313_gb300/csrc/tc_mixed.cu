@@ -440,7 +440,7 @@ constexpr int ST_THREADS = (ST_EPI_WARPS + 2) * 32;  // + producer warp + MMA wa
 constexpr int S_ATILE = 128 * 64;                   // 128 rows x 64 B (32 fp16)
 
 struct SigSmem {
-  uint64_t full[2], empty[2], tfull, tempty;
+  uint64_t full[2], empty[2], col[32], tempty;  // col[c]: K chunk c of the current unit is done
   uint32_t tslot;
   int abort_flag;
   float red[4][128];
@@ -449,7 +449,10 @@ struct SigSmem {
 // The NI output columns are processed in nh parts of NC = NI / nh <= 256 columns (TMEM holds Y1
 // and Y2 of one part: 2 NC <= 512 columns). Work units u = (tau, part h); a unit runs the K
 // chunks c with 32 c < (h + 1) NC, each over the output columns [max(h NC, 32 c), (h + 1) NC)
-// that U and V reach. The epilogue sums d_p over the parts of a tau before writing it.
+// that U and V reach. Output column block j (32 columns) is final once chunk j is done, so the
+// epilogue takes each 16-column block as soon as its chunk completes (barrier col[j]) while the
+// later chunks still run; only the next unit's first chunk waits for the whole epilogue. The
+// epilogue sums d_p over the parts of a tau before writing it.
 __global__ void __launch_bounds__(ST_THREADS, 1)
     k_sig_tc(const __half* __restrict__ XS, const float2* __restrict__ XE, const __half* __restrict__ WS, int ni,
              int nh, int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err) {
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
       mbar_init(&S.full[s], 1);
       mbar_init(&S.empty[s], 1);
     }
-    mbar_init(&S.tfull, 1);
+    for (int c = 0; c < 32; ++c) mbar_init(&S.col[c], 1);
     mbar_init(&S.tempty, ST_EPI_WARPS * 32);
     S.abort_flag = 0;
     fence_mbar_init();
@@ -549,15 +552,16 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
             mma_f16(y2, sdesc_sw64(arl + o), sdesc_sw64(vih + o), idn, 1);
           }
           mma_commit(&S.empty[s]);
-          if (kc == kend - 1) mma_commit(&S.tfull);
+          mma_commit(&S.col[kc]);
         }
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
     // Thread (quad, grp, lane) owns row 32 quad + lane and the 16-column blocks grp, grp + 4, ...
-    // of each part. Its XE values do not depend on tau: a part's first block is fetched before
-    // the wait for the accumulators, each next block while the current one is multiplied.
+    // of each part, taken in column order as their K chunks complete. Its XE values do not
+    // depend on tau: a part's first block is fetched before the first wait, the others after
+    // their chunk completes (the blocks arrive one K chunk apart, which covers the L2 latency).
     const int quad = warp & 3, grp = warp >> 2;  // lane quadrant, column group
     const int row = 32 * quad + lane;
     const int p = pblk * 128 + row;
@@ -572,18 +576,22 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
       float2 xa[16];
 #pragma unroll
       for (int c = 0; c < 16; ++c) xa[c] = grp < nblk ? __ldg(xh + (size_t)(16 * grp + c) * 128) : make_float2(0.f, 0.f);
-      const bool ok = wait_bar(&S.tfull, u & 1, &S.abort_flag, err);
-      tc_fence_after();
-      if (ok) {
-        for (int bk = grp; bk < nblk; bk += 4) {
+      bool ok = true;
+      {
+        for (int bk = grp; bk < nblk && ok; bk += 4) {
           const int n0 = 16 * bk;
+          // the K chunk c that finishes this block's columns runs in parts h' >= h of every tau
+          // (32 c < (h' + 1) NC), so before this unit it has completed tau (nh - h) times
+          ok = wait_bar(&S.col[(h * NC + n0) >> 5], (it * (nh - h)) & 1, &S.abort_flag, err);
+          tc_fence_after();
+          if (!ok) break;
+          if (bk != grp) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) xa[c] = __ldg(xh + (size_t)(n0 + c) * 128);
+          }
           float v1[16], v2[16];
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + n0, v1);
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + NC + n0, v2);
-          float2 xb[16];
-          const bool more = bk + 4 < nblk;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) xb[c] = more ? __ldg(xh + (size_t)(n0 + 64 + c) * 128) : make_float2(0.f, 0.f);
           float part = 0.f;
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -594,8 +602,6 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
           const float bb = s2 - dhi;
           dlo += (dhi - (s2 - bb)) + (part - bb);
           dhi = s2;
-#pragma unroll
-          for (int c = 0; c < 16; ++c) xa[c] = xb[c];
         }
       }
       tc_fence_before();
