@@ -477,21 +477,34 @@ __host__ __device__ constexpr size_t nnls_smem_bytes(int ng) {
 // Real-axis values and QP root, one warp per problem: the 401 scan points are split over
 // the lanes (each lane sums all hats at its own energies); the bisection evaluates one
 // energy per step with the hats split over the lanes and a warp sum.
-// Re sum_m b_m Phi_m(E + i eta) by one thread; the node logarithms are shared between neighbouring hats.
+// Re sum_m b_m Phi_m(E + i eta) by one thread over the hats with b_m != 0; the node logarithms
+// are computed only for the nodes of those hats, and shared between neighbouring hats (a cache
+// of the last three nodes).
 __device__ double resig_cpe_lane(const double* b, const double* x, int ng, double E) {
   const cd z = {E, kEta};
   double s = 0.0;
-  cd l0 = clog_(csub(z, cd{x[0], 0.0})), l1 = clog_(csub(z, cd{x[1], 0.0}));
+  int i0 = -1, i1 = -1, i2 = -1;
+  cd c0{0.0, 0.0}, c1{0.0, 0.0}, c2{0.0, 0.0};
+  auto node_log = [&](int n) {
+    if (n == i2) return c2;
+    if (n == i1) return c1;
+    if (n == i0) return c0;
+    const cd v = clog_(csub(z, cd{x[n], 0.0}));
+    i0 = i1;
+    c0 = c1;
+    i1 = i2;
+    c1 = c2;
+    i2 = n;
+    c2 = v;
+    return v;
+  };
   for (int m = 0; m < ng; ++m) {
-    const cd l2 = clog_(csub(z, cd{x[m + 2], 0.0}));
-    if (b[m] != 0.0) {
-      const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
-      const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
-      const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
-      s += b[m] * (rise.x + fall.x);
-    }
-    l0 = l1;
-    l1 = l2;
+    if (b[m] == 0.0) continue;
+    const cd l0 = node_log(m), l1 = node_log(m + 1), l2 = node_log(m + 2);
+    const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
+    const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
+    const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
+    s += b[m] * (rise.x + fall.x);
   }
   return s;
 }

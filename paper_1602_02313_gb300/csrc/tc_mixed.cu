@@ -397,19 +397,25 @@ __global__ void k_split_x(const double2* __restrict__ Mq, int ni, int np, int np
           make_float2((float)(v.x * kScaleA), (float)(v.y * kScaleA));
   }
   __syncthreads();
-  const int nkc = ni / 32;
-  for (int r = ty; r < 32; r += 8) {
-    const int p = p0 + r, I = I0 + tx;
-    const double2 v = tileS[tx][r];
-    __half rh, rl, ih, il;
-    split2((float)v.x * kScaleA, rh, rl);
-    split2((float)v.y * kScaleA, ih, il);
-    const int pblk = p >> 7, row = p & 127, kc = I >> 5, col = I & 31;
-    const size_t o = sw64_off(row, col) / 2;
-    XS[xs_tile(k, pblk, kc, 0, npb, nkc) + o] = rh;
-    XS[xs_tile(k, pblk, kc, 1, npb, nkc) + o] = rl;
-    XS[xs_tile(k, pblk, kc, 2, npb, nkc) + o] = ih;
-    XS[xs_tile(k, pblk, kc, 3, npb, nkc) + o] = il;
+  // 128 threads write the 32 rows x 4 groups of 8 columns as 16-byte vectors per slice
+  const int t = ty * 32 + tx;
+  if (t < 128) {
+    const int nkc = ni / 32;
+    const int r = t >> 2, g = t & 3;
+    const int p = p0 + r, I = I0 + 8 * g;
+    h8 rh, rl, ih, il;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const double2 v = tileS[8 * g + e][r];
+      split2((float)v.x * kScaleA, rh.v[e], rl.v[e]);
+      split2((float)v.y * kScaleA, ih.v[e], il.v[e]);
+    }
+    const int pblk = p >> 7, row = p & 127, kc = I >> 5;
+    const size_t o = sw64_off(row, I & 31) / 2;
+    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 0, npb, nkc) + o) = rh;
+    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 1, npb, nkc) + o) = rl;
+    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 2, npb, nkc) + o) = ih;
+    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 3, npb, nkc) + o) = il;
   }
 }
 
