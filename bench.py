@@ -350,7 +350,7 @@ def main():
         e2e = {"value": flops_step / dt / 1e12, "unit": "TFLOP/s", "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(eps_h.numel() * 8 + cr.v.nbytes + cr.kmq.nbytes + gr.tau.nbytes),
                "d2h_bytes_per_step": int(out_h.numel() * 8 + sx_h.numel() * 8),
-               "includes": "gw_create (transform matrices, M generated on the GPU from the seed), H2D of eps, "
+               "includes": "gw_create (transform matrices; M generated on the GPU from the seed on a low-priority stream, q by q ahead of its first use), H2D of eps, "
                            "the iteration, D2H of QP energies and Sigma^x, gw_destroy"}
 
     cpu = None

@@ -91,10 +91,13 @@ typedef struct {
                              in its own HBM buffer */
   int q0;                 /* global index of this context's first q (for the generator
                              counter; 0 unless the q points are split over several contexts) */
-  int m_mode;             /* with M == NULL: 0 = generate all q at gw_create when that takes at
-                             most half of the free device memory, else as 2; 1 = all q at
-                             gw_create; 2 = one q at a time, regenerated on first use by a call
-                             that needs M[q] (a crystal whose M does not fit in HBM) */
+  int m_mode;             /* with M == NULL: 0 = as 3 when all q take at most half of the free
+                             device memory, else as 2; 1 = all q generated in gw_create;
+                             2 = one q at a time, regenerated on first use by a call that needs
+                             M[q] (a crystal whose M does not fit in HBM); 3 = all q kept, each
+                             generated on an internal low-priority stream when the q before it
+                             is first used (q = 0 at gw_create), so that generation overlaps
+                             the contractions; calls on the context's stream wait for it */
 } gw_system;
 
 /* Create a context on `device`, ordered on the cudaStream_t `stream` (NULL =

@@ -97,8 +97,32 @@ gw_status launch_gen_m(gw_ctx* c, double* M) {
   return check_launch(c, "gen_m");
 }
 
+// m_lazy: start generating M[iq] on the side stream (once), ordered after nothing else
+static bool m_issue(gw_ctx* c, int iq) {
+  if (iq >= c->nq || c->m_issued[iq]) return true;
+  const uint64_t per_q = (uint64_t)c->nk * c->ni * c->nb * c->nb;
+  // many short blocks on a low-priority stream: the contraction kernels' blocks are scheduled
+  // first, these fill the room they leave
+  const uint64_t nblk = (per_q + 256 * 16 - 1) / (256 * 16);
+  k_gen_m<<<(unsigned)nblk, 256, 0, c->m_stream>>>((double2*)c->d_M_own + (size_t)iq * per_q, per_q,
+                                                   (uint64_t)(c->q0 + iq) * per_q, c->seed, std::sqrt(0.5 / c->nb));
+  if (check_launch(c, "gen_m") != GW_OK) return false;
+  if (cudaEventRecord(c->m_done[iq], c->m_stream) != cudaSuccess) return false;
+  c->m_issued[iq] = 1;
+  return true;
+}
+
 const double* m_block(gw_ctx* c, int iq) {
   const uint64_t per_q = (uint64_t)c->nk * c->ni * c->nb * c->nb;
+  if (c->m_lazy) {
+    // the block of iq must be done before the context's stream uses it; the next q's block is
+    // generated meanwhile (FP64-pipe work that runs beside the tensor-core contractions)
+    if (!m_issue(c, iq) || cudaStreamWaitEvent(c->stream, c->m_done[iq], 0) != cudaSuccess || !m_issue(c, iq + 1)) {
+      set_err(c, GW_ECUDA, "M generation");
+      return nullptr;
+    }
+    return c->d_M + 2 * (size_t)iq * per_q;
+  }
   if (!c->m_per_q) return c->d_M + 2 * (size_t)iq * per_q;
   if (c->m_cur != iq) {
     k_gen_m<<<152 * 8, 256, 0, c->stream>>>((double2*)c->d_M_own, per_q, (uint64_t)(c->q0 + iq) * per_q, c->seed,
@@ -517,13 +541,31 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
       free_b = 0;
     }
     c->m_per_q = s->m_mode == 2 || (s->m_mode == 0 && bytes > free_b / 2);
+    c->m_lazy = !c->m_per_q && (s->m_mode == 0 || s->m_mode == 3);
     if (cudaMalloc((void**)&c->d_M_own, c->m_per_q ? per_q : bytes) != cudaSuccess) {
       cudaGetLastError();
       gw_destroy(c);
       return GW_ENOMEM;
     }
     c->d_M = c->d_M_own;
-    if (!c->m_per_q && (st = launch_gen_m(c, c->d_M_own)) != GW_OK) {
+    if (c->m_lazy) {
+      c->m_done.assign(c->nq, nullptr);
+      c->m_issued.assign(c->nq, 0);
+      int prio_low = 0, prio_high = 0;
+      cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+      bool okc = cudaStreamCreateWithPriority(&c->m_stream, cudaStreamNonBlocking, prio_low) == cudaSuccess;
+      for (int q = 0; q < c->nq && okc; ++q)
+        okc = cudaEventCreateWithFlags(&c->m_done[q], cudaEventDisableTiming) == cudaSuccess;
+      if (!okc) {
+        cudaGetLastError();
+        gw_destroy(c);
+        return GW_ECUDA;
+      }
+      if (!m_issue(c, 0)) {  // the first block starts at once
+        gw_destroy(c);
+        return GW_ECUDA;
+      }
+    } else if (!c->m_per_q && (st = launch_gen_m(c, c->d_M_own)) != GW_OK) {
       gw_destroy(c);
       return st;
     }
@@ -542,6 +584,11 @@ gw_status gw_destroy(gw_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   cudaDeviceSynchronize();
   kt_clear(c);
+  for (cudaEvent_t e : c->m_done)
+    if (e) cudaEventDestroy(e);
+  c->m_done.clear();
+  if (c->m_stream) cudaStreamDestroy(c->m_stream);
+  c->m_stream = nullptr;
   double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
                     c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_b,
                     c->d_pade,  c->d_vm};

@@ -70,6 +70,10 @@ struct gw_ctx {
   double* d_M_own = nullptr;
   bool m_per_q = false;        // M generated one q at a time into d_M_own
   int m_cur = -1;              // the q whose block d_M_own holds (m_per_q)
+  bool m_lazy = false;         // all q kept, each generated on a side stream ahead of first use
+  cudaStream_t m_stream = nullptr;
+  std::vector<cudaEvent_t> m_done;  // [nq]: generation of M[q] finished (m_lazy)
+  std::vector<char> m_issued;       // [nq]
   double* d_Bfwd = nullptr;    // cplx [nnu][ntau]
   double* d_Ffwd = nullptr;    // cplx [nw][ntau]
   double* d_Fcont = nullptr;   // cplx [ncont][ntau]
