@@ -176,6 +176,40 @@ def _config(cfg, args, prec):
             "l2": "inputs larger than L2 (M tensor 69 GB, P/W per q 50 MB each)"}
 
 
+def run_batch(args, prec):
+    """Twelve heterogeneous crystals (gwinputs.batch_crystals): one GW iteration of all of them
+    launched call by call, crystal after crystal, against one replay of the autotuned CUDA graph.
+    Not the headline workload; one GPU."""
+    import torch
+
+    import gwinputs as gi
+    from paper_1602_02313_gb300.batched import Batch
+    systems = gi.batch_crystals()
+    batch = Batch(systems, omega=args.omega, prec=prec, qb=2)
+    tuning = batch.tune_kernels()
+    crystal_ms = batch.time_crystals()
+    for _ in range(max(0, args.warmup - 1)):
+        batch.run_sequential()
+    seq_ms = batch.time_sequential(reps=args.steps)
+    sched = batch.tune_schedule(branch_choices=(1, 2, 3, 4, 6, 12), reps=1)
+    graph_ms = batch.time_graph(batch.graph, reps=args.steps)
+    batch.check()
+    shapes = [f"Nk={cr.nk} Nb={cr.nb} NI={cr.ni} Ntau={len(gr.tau)} beta={gr.beta}" for cr, gr in systems]
+    out = {"metric": METRIC + " (batch of 12 crystals)", "value": batch.flops / (graph_ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms,
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "fp16x2 split (fp32 accum) + f64",
+           "data": "synthetic",
+           "config": {"workload": "batch of 12 heterogeneous synthetic crystals: " + "; ".join(shapes),
+                      "sequential_ms": seq_ms, "graph_ms": graph_ms, "speedup_vs_sequential": seq_ms / graph_ms,
+                      "branches": batch.nbranch, "graph_ms_by_branches": sched,
+                      "crystal_ms": crystal_ms, "pol_tuning": tuning, "continuation": "cpe",
+                      "l2": "inputs larger than L2"},
+           "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(out))
+    batch.close()
+    torch.cuda.synchronize()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,6 +253,8 @@ def main():
     if world > 1:
         dist.barrier()
     prec = gw.PREC[args.prec]
+    if args.config == "batch12":
+        return run_batch(args, prec)
     full, gr = gi.make_config(args.config, **({"nk": args.nk} if args.nk > 0 else {}))
     nq = full.nq if args.nq <= 0 else min(args.nq, full.nq)
     q0, cnt = q_range(nq, rank, world)

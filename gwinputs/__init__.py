@@ -349,3 +349,24 @@ def make_config(name, **over):
                       qlist=c["qlist"] if c["qlist"] is not None else list(range(c["nk"])))
     gr = make_grid(c["beta"], c["ntau"], c["nnu"], c["nw"], ncont=c.get("ncont", 128))
     return cr, gr
+
+
+def batch_crystals(n=12, seed=4000, nb_choices=(32, 64, 96, 128), nk_choices=(8, 27), ntau_choices=(32, 48, 64),
+                   beta_range=(100.0, 500.0), nb_max_at_nk27=64):
+    """A seeded batch of heterogeneous synthetic crystals (the batched-launch workload): per
+    crystal, Nb from nb_choices, NI = 4 Nb, Nb / 2 occupied, Nk from nk_choices (the larger
+    k-mesh only up to Nb = nb_max_at_nk27, which bounds the M tensors to a few tens of GB in
+    total), q on the k grid, Ntau = Nnu = Nw from ntau_choices, beta uniform in beta_range.
+    Crystal i has seed `seed + 1 + i`. Returns a list of (Crystal, Grid)."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    out = []
+    for i in range(n):
+        nb = int(rng.choice(nb_choices))
+        nks = [k for k in nk_choices if k == min(nk_choices) or nb <= nb_max_at_nk27]
+        nk = int(rng.choice(nks))
+        ntau = int(rng.choice(ntau_choices))
+        beta = float(np.round(rng.uniform(*beta_range), 1))
+        cr = make_crystal(seed + 1 + i, nk, nb, nb // 2, 4 * nb, beta, qlist=list(range(nk)))
+        gr = make_grid(beta, ntau, ntau, ntau, ncont=128)
+        out.append((cr, gr))
+    return out

@@ -263,6 +263,20 @@ int64_t gw_launch_count(gw_ctx* ctx);
  * gw_kernel_time synchronises the stream and returns the summed device time (ms) and the
  * number of recorded launches of the named kernel. No device memory is allocated. */
 gw_status gw_kernel_timing(gw_ctx* ctx, int enable);
+
+/* Moves the context to another cudaStream_t (same device) for the calls that follow; work
+ * already queued stays on the old stream (the caller orders the two). Lets one context serve as
+ * a branch of a multi-stream CUDA graph. NULL = the legacy default stream. */
+gw_status gw_set_stream(gw_ctx* ctx, void* stream);
+
+/* Schedule knobs of the tensor-core polarization, for the autotuner of the batched driver.
+ *  GW_TUNE_POL_SEG_CHUNKS: K chunks (32 pairs each) summed in one FP32 accumulator segment,
+ *      1 .. 32 (default 32; fewer = more, smaller partials and a smaller accumulation error);
+ *  GW_TUNE_POL_PART_MB: MiB of FP32 partial strips held at once (default 8192; the K segments
+ *      run in passes beyond it), >= 1.
+ * Out-of-range values return GW_EINVAL. Results stay within the tensor-core error bound. */
+typedef enum { GW_TUNE_POL_SEG_CHUNKS = 0, GW_TUNE_POL_PART_MB = 1 } gw_tune;
+gw_status gw_set_tuning(gw_ctx* ctx, gw_tune key, int64_t value);
 gw_status gw_kernel_time(gw_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 
 /* Host-only (no GPU needed): the transform matrices gw_create builds for `grid`,

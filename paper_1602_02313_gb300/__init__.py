@@ -24,6 +24,7 @@ GW_FP64, GW_FP16X2, GW_BF16X3, GW_F32X2 = 0, 1, 2, 3
 GW_BOSE, GW_FERMI = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU, GW_TAU_TO_IW_CONT = 0, 1, 2
 GW_PADE, GW_CPE = 0, 1
+GW_TUNE_POL_SEG_CHUNKS, GW_TUNE_POL_PART_MB = 0, 1
 PREC = {"fp64": GW_FP64, "fp16x2": GW_FP16X2, "bf16x3": GW_BF16X3}
 
 _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW_ESINGULAR",
@@ -33,7 +34,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
-           "gw_kernel_timing", "gw_kernel_time",
+           "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
            "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_get_params", "gw_mlp_set_params",
            "gw_cpe_features", "gw_cpe_fit_matrix", "gw_cpe_seed", "gw_cpe_iterations"]
@@ -111,6 +112,8 @@ def load_library(path=LIB_PATH):
         "gw_transform_matrices": [ctypes.POINTER(_Grid), vp, vp, vp, vp, vp],
         "gw_launch_count": [vp],
         "gw_kernel_timing": [vp, i32],
+        "gw_set_stream": [vp, vp],
+        "gw_set_tuning": [vp, i32, i64],
         "gw_kernel_time": [vp, ctypes.c_char_p, vp, vp],
         "gw_screen_static": [i32, i32, i32, vp, vp, vp, vp, vp],
         "gw_mlp_create": [ctypes.POINTER(vp), i32, i32, i32, i32, ctypes.c_uint64, i32, vp],
@@ -206,6 +209,14 @@ class GW:
 
     def launch_count(self):
         return int(self.lib.gw_launch_count(self.h))
+
+    def set_stream(self, stream):
+        """Queue the following calls on `stream` (a torch.cuda.Stream on the context's device)."""
+        self._check(self.lib.gw_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "gw_set_stream")
+        self.stream = stream
+
+    def set_tuning(self, key, value):
+        self._check(self.lib.gw_set_tuning(self.h, int(key), int(value)), "gw_set_tuning")
 
     def kernel_timing(self, enable=True):
         """Record CUDA events around the tensor-core and screening launches from now on."""

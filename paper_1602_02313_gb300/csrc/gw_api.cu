@@ -615,6 +615,27 @@ const char* gw_last_error(gw_ctx* c) { return c ? c->err.c_str() : "null context
 
 int64_t gw_launch_count(gw_ctx* c) { return c ? c->launches : -1; }
 
+gw_status gw_set_stream(gw_ctx* c, void* stream) {
+  if (!c) return GW_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return GW_OK;
+}
+
+gw_status gw_set_tuning(gw_ctx* c, gw_tune key, int64_t value) {
+  if (!c) return GW_EINVAL;
+  switch (key) {
+    case GW_TUNE_POL_SEG_CHUNKS:
+      if (value < 1 || value > 32) return set_err(c, GW_EINVAL, "gw_set_tuning: segment chunks in 1 .. 32");
+      c->pol_seg_chunks = (int)value;
+      return GW_OK;
+    case GW_TUNE_POL_PART_MB:
+      if (value < 1 || value > (1ll << 22)) return set_err(c, GW_EINVAL, "gw_set_tuning: partial MiB >= 1");
+      c->pol_part_bytes = (size_t)value << 20;
+      return GW_OK;
+  }
+  return set_err(c, GW_EINVAL, "gw_set_tuning: unknown key");
+}
+
 gw_status gw_kernel_timing(gw_ctx* c, int enable) {
   if (!c) return GW_EINVAL;
   kt_clear(c);

@@ -37,8 +37,9 @@ struct MixedWork {
   size_t mslices_bytes = 0;
   void* wslices = nullptr;    // per-tau split copies of W~ (Sigma) or scaled rows (P)
   size_t wslices_bytes = 0;
-  double* dacc = nullptr;     // FP64 partial sums
+  double* dacc = nullptr;     // P strip metadata (uploaded once per context) and error word
   size_t dacc_bytes = 0;
+  bool strips_ready = false;
 };
 
 }  // namespace gwi
@@ -105,6 +106,8 @@ struct gw_ctx {
   size_t pade_bytes = 0;
   // tensor-core path
   gwi::MixedWork mw;
+  int pol_seg_chunks = 32;                  // K chunks per FP32 accumulation segment of P (<= 32)
+  size_t pol_part_bytes = 8ull << 30;       // FP32 partial strips of P held at once
   // per-kernel timing (gw_kernel_timing): CUDA events recorded around selected launches
   struct KernelEvents {
     const char* name;

@@ -75,8 +75,7 @@ struct alignas(16) h8 {
 //   YS[k][chunk][iblk][slice][128 rows x 128 B], row = [Re A (32 pairs) | Im A (32 pairs)],
 // slices hi, lo. The scaled operand X = w_tau(p) A (rows of the strip) is built by the
 // producer warps from the same image. TMEM holds Re P (N columns) and Im P (N columns).
-constexpr int kPolChunksPerSeg = 32;
-constexpr size_t kPolPartBytes = 8ull << 30;  // at most 8 GiB of FP32 partial strips at once
+constexpr int kPolChunksPerSeg = 32;  // upper bound of the context's K chunks per segment
 constexpr int PT_THREADS = 288;                     // warps 0-7 produce / run the epilogue, warp 8 issues MMAs
 constexpr int P_XT = 16384;                         // one X slice: 128 rows x 128 B
 constexpr int P_STAGE_BYTES = 2 * P_XT + 2 * 256 * 128;  // X hi, lo (128 rows) + Y hi, lo (<= 256 rows)
@@ -681,16 +680,18 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   const int np = c->nb * c->nb, cpk = (np + 31) / 32, total = c->nk * cpk, npw = cpk * 32;
   // K segments. The tensor cores accumulate in FP32 with an error that grows with the
   // number of MMAs chained into one accumulator (measured ~2^-24 per MMA, biased), so
-  // each work unit covers at most kPolChunksPerSeg chunks of 32 pairs (384 chained MMAs);
+  // each work unit covers at most the context's pol_seg_chunks <= kPolChunksPerSeg chunks of
+  // 32 pairs (384 chained MMAs at 32);
   // the FP32 partial strips are summed in FP64 afterwards.
   const int sms = num_sms(c);
   const int base_units = nstrips * c->ntau;
-  int nseg = std::max(1, (total + kPolChunksPerSeg - 1) / kPolChunksPerSeg);
+  const int seg_chunks = std::max(1, std::min(c->pol_seg_chunks, kPolChunksPerSeg));
+  int nseg = std::max(1, (total + seg_chunks - 1) / seg_chunks);
   while (base_units * nseg < 2 * sms && (total + nseg) / (nseg + 1) >= 4) ++nseg;
-  // the partials of at most kPolPartBytes are held at once: segments run in passes, each
+  // the partials of at most pol_part_bytes are held at once: segments run in passes, each
   // reduced into P (the first pass writes, later ones add)
   const size_t seg_bytes = (size_t)base_units * 2 * 128 * 256 * sizeof(float);
-  const int seg_pass = (int)std::max<size_t>(1, std::min<size_t>(nseg, kPolPartBytes / seg_bytes));
+  const int seg_pass = (int)std::max<size_t>(1, std::min<size_t>(nseg, c->pol_part_bytes / seg_bytes));
   const size_t part_bytes = seg_bytes * seg_pass;
   const size_t wt_bytes = (size_t)c->nk * c->ntau * npw * sizeof(float);
   const size_t ys_bytes = (size_t)c->nk * cpk * nib * 2 * 128 * 64 * sizeof(__half);
@@ -701,12 +702,18 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   float* d_wt = d_part + part_bytes / sizeof(float);
   __half* d_ys = (__half*)((char*)d_wt + wt_bytes);
   const size_t meta_bytes = sizeof(int4) * strips.size() + sizeof(int) * strip_of.size() + sizeof(int);
+  const void* meta_before = c->mw.dacc;
   if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P strips")) != GW_OK) return st;
+  if (c->mw.dacc != meta_before) c->mw.strips_ready = false;
   int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
   int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
   int* d_err = d_strip_of + strip_of.size();
-  cudaMemcpyAsync(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice, c->stream);
+  if (!c->mw.strips_ready) {  // depends on ni only: uploaded on the first call
+    if (cudaMemcpy(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return set_err(c, GW_ECUDA, "P strips upload");
+    c->mw.strips_ready = true;
+  }
   cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   if (ni % 128) cudaMemsetAsync(d_ys, 0, ys_bytes, c->stream);  // rows >= ni of the last block stay zero
   const double2* Mq = (const double2*)m_block(c, iq);
