@@ -173,7 +173,8 @@ def _config(cfg, args, prec):
                         f"({c['nocc']} occ), NI={c['ni']}, Ntau={c['ntau']}, Nnu=Nw={c['nnu']}, beta={c['beta']}",
             "precision": prec, "omega": args.omega, "continuation": getattr(args, "cont", "pade"),
             "parallelism": f"q-split over {args.gpus} GPU(s)",
-            "l2": "inputs larger than L2 (M tensor 69 GB, P/W per q 50 MB each)"}
+            "l2": "inputs larger than L2 (M tensor %.1f GB per q, P(tau) and W~(tau) %.0f MB per q each)" % (
+                c["nk"] * c["ni"] * c["nb"] ** 2 * 16 / 1e9, c["ntau"] * c["ni"] ** 2 * 16 / 1e6)}
 
 
 def run_batch(args, prec):
