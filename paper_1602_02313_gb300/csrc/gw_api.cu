@@ -467,7 +467,7 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
   if (!out || !g || !s) return GW_EINVAL;
   *out = nullptr;
   if (!grid_ok(g)) return GW_EINVAL;
-  if (s->q0 < 0 || s->nk < 1 || s->nq < 1 || s->nb < 1 || s->nb > 256 || s->ni < 16 || s->ni > 1024 || (s->ni % 32) || !s->kmq ||
+  if (s->m_mode < 0 || s->m_mode > 3 || s->q0 < 0 || s->nk < 1 || s->nq < 1 || s->nb < 1 || s->nb > 256 || s->ni < 16 || s->ni > 1024 || (s->ni % 32) || !s->kmq ||
       !s->v || !(s->omega > 0))
     return GW_EINVAL;
   for (int i = 0; i < s->nq * s->nk; ++i)

@@ -68,4 +68,11 @@ def test_invalid_arguments_rejected_on_host(gw):
     h = ctypes.c_void_p()
     assert lib.gw_create(ctypes.byref(h), ctypes.byref(gs), ctypes.byref(s), 0, None) == gw.GW_EINVAL
     assert lib.gw_create(None, ctypes.byref(gs), ctypes.byref(s), 0, None) == gw.GW_EINVAL
+    v32 = np.ones((1, 32))
+    s = gw._System(1, 8, 1, 16, 8, 32, 1.0, kmq.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                   v32.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 0, 7)  # no M mode 7
+    assert lib.gw_create(ctypes.byref(h), ctypes.byref(gs), ctypes.byref(s), 0, None) == gw.GW_EINVAL
     assert lib.gw_sync(None) == gw.GW_EINVAL
+    assert lib.gw_set_stream(None, None) == gw.GW_EINVAL
+    assert lib.gw_set_tuning(None, gw.GW_TUNE_POL_SEG_CHUNKS, 16) == gw.GW_EINVAL
+    assert lib.gw_kernel_timing(None, 1) == gw.GW_EINVAL

@@ -22,6 +22,10 @@ def test_batch_graph_matches_sequential(gw):
     from paper_1602_02313_gb300.batched import Batch
     systems = gi.batch_crystals(n=4, seed=4100, nb_choices=(16, 32), nk_choices=(8,), ntau_choices=(16, 24))
     batch = Batch(systems, omega=gi.OMEGA_SI, qb=2)
+    with pytest.raises(gw.GwError):
+        batch.ctxs[0].set_tuning(gw.GW_TUNE_POL_SEG_CHUNKS, 33)  # beyond the FP32 accumulation bound
+    with pytest.raises(gw.GwError):
+        batch.ctxs[0].set_tuning(gw.GW_TUNE_POL_PART_MB, 0)
     tuning = batch.tune_kernels(seg_choices=(32, 8), part_mb_choices=(64, 1))
     assert all(v["seg_chunks"] in (32, 8) for v in tuning.values())
     ms = batch.time_crystals()
