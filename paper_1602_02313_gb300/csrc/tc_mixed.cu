@@ -10,9 +10,9 @@
 //   P_II'(tau) = pref sum_{k,p} w_p(tau) A_k[I,p] conj(A_k[I',p]),  w_p = -G_b(k|tau) G_a(k-q|beta-tau)
 //   Re P = X Y^T, Im P = X' Y^T with rows X_I = [w Re A_I | w Im A_I], Y_I' = [Re A_I' | Im A_I'],
 //   X'_I = [w Im A_I | -w Re A_I] (same shared-memory tile, other K halves, negated).
-//   Work unit = (K segment, 128 x 128 output tile with ti <= tj, pair of tau); FP32 partial
-//   tiles are summed over K segments in FP64 by a second kernel, which also mirrors the
-//   Hermitian lower triangle.
+//   Work unit = (K segment, 128-row strip of <= 256 columns of the upper triangle, tau); the
+//   FP32 partial strips are summed over K segments with float-float accumulators by a second
+//   kernel, which also writes the Hermitian lower triangle.
 //
 // self-energy, Eq. (sigc), one q:
 //   d_p(tau) = a_p^H W~(tau) a_p = Re a_p^T Wr Re a_p + Im a_p^T Wr Im a_p + 2 Im a_p^T Wi Re a_p
@@ -278,8 +278,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
     const int row = 32 * quad + lane;
     float* out = part + (size_t)u * 2 * 128 * 256;
     const int nb16 = N / 16;
+    const int ab = 4 * xb + quad;  // the 32-row block of this warp's rows
     for (int acc = 0; acc < 2; ++acc) {
       for (int bk = half; bk < nb16; bk += 2) {
+        if (((c0 + 16 * bk) >> 5) < ab) continue;  // below the diagonal: never read back
         float v[16];
         if (ok) {
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + acc * N + 16 * bk, v);
