@@ -167,7 +167,8 @@ gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, gw_prec p
  * All calls on a device share the one array and it keeps the last call's contents, so calls
  * that overlap on the GPU (different streams, or concurrent host threads) race; the solve
  * overwrites every scratch element it reads, so nothing needs clearing between calls.
- * Computes exactly what gw_screen does, for nq q points at once:
+ * Computes what gw_screen with GW_FP64 does (by elimination of [1 - Pi | Pi] in FP64; the
+ * results agree to rounding), for nq q points at once:
  * sqrt_v (device) [nq][ni] = v_I(q)^(1/2); P_iv, Wt_iv cplx [nq][nnu][ni][ni]; info [nq][nnu].
  * Returns GW_EINVAL if one q point's systems (nnu * ni * 2 ni * 16 bytes) exceed 128 MiB,
  * GW_ECUDA on a launch error; runs on the cudaStream_t `stream` (NULL = legacy stream). */

@@ -684,7 +684,7 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   // number of MMAs chained into one accumulator (measured ~2^-24 per MMA, biased), so
   // each work unit covers at most the context's pol_seg_chunks <= kPolChunksPerSeg chunks of
   // 32 pairs (384 chained MMAs at 32);
-  // the FP32 partial strips are summed in FP64 afterwards.
+  // the FP32 partial strips are summed afterwards with float-float accumulators.
   const int sms = num_sms(c);
   const int base_units = nstrips * c->ntau;
   const int seg_chunks = std::max(1, std::min(c->pol_seg_chunks, kPolChunksPerSeg));

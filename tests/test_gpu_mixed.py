@@ -3,7 +3,7 @@ against the FP64 oracle and the FP64 GPU path, called through the C ABI.
 
 Error bars of the split-precision path: each operand carries 22 significant
 bits (two fp16 slices); the accumulation runs in FP32 in tensor memory over
-K segments and is summed in FP64 across segments. The expected max-norm
+K segments and is summed across segments with float-float (two-sum) accumulators. The expected max-norm
 relative error is therefore ~sqrt(n_acc) * 2^-24 with n_acc the number of
 FP32 accumulation steps per output (a few 1e-6 at the bench sizes); the
 tolerances below are set from that bound.
