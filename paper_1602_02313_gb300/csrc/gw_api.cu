@@ -83,9 +83,10 @@ __global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t off, uint6
     const double u1 = ((double)m1 + 1.0) * 0x1p-53;
     const double u2 = (double)m2 * 0x1p-53;
     const double r = sqrt(-2.0 * log(u1));
-    const double th = 6.283185307179586 * u2;
+    // theta = 2 pi u2; sincospi takes theta / pi = 2 u2 exactly (no range reduction by pi),
+    // which differs from rounding 2 pi u2 first by < 1e-15
     double s, co;
-    sincos(th, &s, &co);
+    sincospi(2.0 * u2, &s, &co);
     M[idx] = make_double2(r * co * scale, r * s * scale);
   }
 }
