@@ -55,3 +55,17 @@ def test_grid_structure():
     assert abs(g.wtau.sum() - (g.beta - 2e-3)) < 1e-9
     assert len(set(g.nu_idx.tolist())) == len(g.nu_idx) and g.nu_idx.min() >= 0
     assert 1 <= g.npole <= g.ntau
+
+
+def test_batch_crystals_respect_the_caps_and_are_reproducible():
+    import gwinputs as gi
+    a = gi.batch_crystals(n=5, seed=4200, nb_choices=(16, 32, 64), nk_choices=(8, 27), ntau_choices=(16, 24),
+                          nb_max_at_nk27=16)
+    b = gi.batch_crystals(n=5, seed=4200, nb_choices=(16, 32, 64), nk_choices=(8, 27), ntau_choices=(16, 24),
+                          nb_max_at_nk27=16)
+    for (cr, gr), (cr2, gr2) in zip(a, b):
+        assert cr.nb in (16, 32, 64) and cr.ni == 4 * cr.nb and cr.nocc == cr.nb // 2
+        assert cr.nk in (8, 27) and (cr.nk == 8 or cr.nb <= 16)
+        assert cr.nq == cr.nk and len(gr.tau) in (16, 24) and 100.0 <= gr.beta <= 500.0
+        assert (cr.eps == cr2.eps).all() and (cr.v == cr2.v).all() and gr.beta == gr2.beta
+    assert len({cr.seed for cr, _ in a}) == 5
