@@ -39,7 +39,7 @@ class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
     def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-3, mlp=None,
-                 nfit=64, screen_prec=None):
+                 nfit=64, screen_prec=None, keep_w=False):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
@@ -68,6 +68,8 @@ class Chain:
         self.info = torch.zeros(self.qb, self.nnu, dtype=torch.int32, **d)
         self.Siw = torch.zeros(nk, nb, self.nw, dtype=c16, **d)
         self.Siwc = torch.zeros(nk, nb, self.ncont, dtype=c16, **d)
+        # GW0 (Sec. III.B, after Eq. dysong): W~(tau) of every q kept from the first pass
+        self.Wkeep = torch.zeros(len(self.iqs), nt, ni, ni, dtype=c16, **d) if keep_w else None
         self.G1 = torch.zeros_like(self.G)
         self.occ1 = torch.zeros_like(self.occ)
         self.eqp = torch.zeros(nk * nb, dtype=f8, **d)
@@ -121,7 +123,16 @@ class Chain:
                        self.screen_prec)
             for j, iq in enumerate(batch):
                 ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt, self.screen_prec)
+                if self.Wkeep is not None:
+                    self.Wkeep[b0 + j].copy_(self.Wt)
                 self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))
+
+    def sigma_fixed_w(self, G, occ):
+        """Sigma^c(tau), Sigma^x from G with the W~(tau) kept by the first pass (GW0)."""
+        self.S.zero_()
+        self.Sx.zero_()
+        for j, iq in enumerate(self.iqs):
+            self.ctx.selfenergy(iq, G, occ, self.Wkeep[j], self.S, self.Sx, self.prec)
 
     def finish(self, vxc=None):
         """Sigma(i w), Dyson update, continuation and QP energies from the summed Sigma."""
@@ -147,15 +158,21 @@ class Chain:
         self.finish()
         self.vxc = self.Sx.clone()  # Sigma_0 = Sigma^x[G0], kept fixed by the later passes
 
-    def iterate(self, n):
+    def iterate(self, n, gw0=False):
         """n self-consistent passes after step(): P, W~ and Sigma from the previous pass's
         dressed G (Eqs. dysongf-zcjk solved in i w), the Dyson update from the band energies
-        with the new Sigma and the fixed reference potential."""
+        with the new Sigma and the fixed reference potential. gw0=True keeps W~ of the first
+        pass (the chain must be built with keep_w=True) and updates only G and Sigma."""
         if self.vxc is None:
             raise GwError("Chain.iterate: run step() first")
+        if gw0 and self.Wkeep is None:
+            raise GwError("Chain.iterate: GW0 needs a chain built with keep_w=True")
         for _ in range(n):
             G, occ = self.G1.clone(), self.occ1.clone()
-            self.sigma(G, occ)
+            if gw0:
+                self.sigma_fixed_w(G, occ)
+            else:
+                self.sigma(G, occ)
             self.finish(self.vxc)
 
     def check(self):

@@ -374,6 +374,29 @@ def test_scgw_two_passes_small(gw, small):
     assert rel(host(ch.occ1), f) < TOL  # -G(beta^-) of the dressed G: O(1) to O(10) here
 
 
+def test_gw0_two_passes_small(gw, small):
+    """G0W0 then one GW0 pass (W~ kept from the first pass, Sigma from the dressed G), FP64 chain on
+    the GPU against the oracle."""
+    from paper_1602_02313_gb300.driver import Chain
+    cr, gr, ctx = small
+    ch = Chain(ctx, dev(cr.eps), prec=gw.GW_FP64, qb=1, cont_method=gw.GW_PADE, keep_w=True)
+    ch.step()
+    ch.iterate(1, gw0=True)
+    ch.check()
+    M = gi.m_for_q(cr, 0)
+    G, f = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    Wt = orc.nu_to_tau(orc.screen(orc.tau_to_nu(orc.polarization(M, G, cr.kmq[0]), gr), cr.v[0]), gr)
+    S, Sx, _ = orc.selfenergy(M, G, Wt, cr.v[0], cr.kmq[0], f)
+    vxc = Sx
+    G, f = orc.dyson_iw(cr.eps, Sx, vxc, orc.sigma_tau_to_iw(S, gr), gr)
+    S, Sx, _ = orc.selfenergy(M, G, Wt, cr.v[0], cr.kmq[0], f)  # same W~
+    G, f = orc.dyson_iw(cr.eps, Sx, vxc, orc.sigma_tau_to_iw(S, gr), gr)
+    assert rel(host(ch.S), S) < TOL
+    assert rel(host(ch.Sx), Sx) < TOL
+    assert rel(host(ch.G1), G) < TOL
+    assert rel(host(ch.occ1), f) < TOL
+
+
 # ------------------------------------------------------------------ full size (Nk=64, Nb=64, NI=256), sampled
 def test_c2_full_size_sampled(gw):
     """The bench workload's sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): FP64 P of
