@@ -567,8 +567,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
     // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
     // Thread (quad, grp, lane) owns row 32 quad + lane and the 16-column blocks grp, grp + 4, ...
     // of each part, taken in column order as their K chunks complete. Its XE values do not
-    // depend on tau: a part's first block is fetched before the first wait, the others after
-    // their chunk completes (the blocks arrive one K chunk apart, which covers the L2 latency).
+    // depend on tau: each block's are fetched before the wait for its chunk.
     const int quad = warp & 3, grp = warp >> 2;  // lane quadrant, column group
     const int row = 32 * quad + lane;
     const int p = pblk * 128 + row;
@@ -587,15 +586,15 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
       {
         for (int bk = grp; bk < nblk && ok; bk += 4) {
           const int n0 = 16 * bk;
+          if (bk != grp) {  // in flight while this block's chunk completes
+#pragma unroll
+            for (int c = 0; c < 16; ++c) xa[c] = __ldg(xh + (size_t)(n0 + c) * 128);
+          }
           // the K chunk c that finishes this block's columns runs in parts h' >= h of every tau
           // (32 c < (h' + 1) NC), so before this unit it has completed tau (nh - h) times
           ok = wait_bar(&S.col[(h * NC + n0) >> 5], (it * (nh - h)) & 1, &S.abort_flag, err);
           tc_fence_after();
           if (!ok) break;
-          if (bk != grp) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) xa[c] = __ldg(xh + (size_t)(n0 + c) * 128);
-          }
           float v1[16], v2[16];
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + n0, v1);
           tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + NC + n0, v2);
