@@ -346,6 +346,19 @@ def main():
         kname = dom
         achieved = per_launch_flops[dom] / (kt[dom] * 1e-3) / 1e12 if dom in kt else None
         label = "gw_" + dom + " (whole call)"
+    # the float-float screening against the measured float-float rate of the FP32 pipes:
+    # NI^3 complex multiply-adds per (q, nu) system (in-place Gauss-Jordan inverse)
+    roof_alu = None
+    if "k_screen_inv" in kern and prec != gw.GW_FP64:
+        fp64_tf, fp32_tf = gw.measure_alu(local)
+        macs = float(cr.ni) ** 3 * len(chain.iqs) * len(gr.nu_idx) * args.steps
+        ach = macs / (kern["k_screen_inv"]["total_ms"] * 1e-3) / 1e9
+        peak_ff = fp32_tf * 1e3 / 96.0  # 48 FP32-pipe operations (2 flops each) per complex MAC
+        roof_alu = {"bound": "alu", "kernel": "k_screen_inv<float-float> (CUDA events around each launch)",
+                    "achieved": ach, "peak": peak_ff, "unit": "G complex float-float MAC/s", "frac": ach / peak_ff,
+                    "peak_source": "measured FP32 FMA rate of this GPU (gw_measure_alu, this run) / 48 operations "
+                                   "per float-float complex multiply-add",
+                    "measured_fp64_tflops": fp64_tf, "measured_fp32_tflops": fp32_tf}
     roof = {"bound": "tensor" if prec != gw.GW_FP64 else "alu", "kernel": label,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": _traffic(kname),
@@ -401,7 +414,7 @@ def main():
                "vs_baseline": None, "dtype": {"fp16x2": "fp16x2 split (fp32 accum) + f64",
                                               "fp64": "f64"}[args.prec],
                "data": "synthetic", "config": _config(args.config, args, args.prec) | {"nq": nq, "nk": cr.nk},
-               "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "e2e": e2e,
+               "gpu_launches": int(launches), "clocks": clocks, "roofline": roof, "roofline_alu": roof_alu, "e2e": e2e,
                "cpu_baseline": cpu}
         print(json.dumps(out))
     if world > 1:

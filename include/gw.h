@@ -265,6 +265,13 @@ int64_t gw_launch_count(gw_ctx* ctx);
  * number of recorded launches of the named kernel. No device memory is allocated. */
 gw_status gw_kernel_timing(gw_ctx* ctx, int enable);
 
+/* Measured rates of the CUDA-core pipes on `device` (no context needed; runs two short
+ * kernels of independent FMA chains): native FP64 and FP32 FMA throughput, TFLOP/s. A
+ * float-float complex multiply-add (the mixed chain's screening and bosonic transforms) is 48
+ * FP32-pipe operations, so fp32_tflops / 96 * 1e3 G/s is those kernels' ALU roofline.
+ * Allocates 64 bytes. */
+gw_status gw_measure_alu(int device, double* fp64_tflops, double* fp32_tflops);
+
 /* Moves the context to another cudaStream_t (same device) for the calls that follow; work
  * already queued stays on the old stream (the caller orders the two). Lets one context serve as
  * a branch of a multi-stream CUDA graph. NULL = the legacy default stream. */

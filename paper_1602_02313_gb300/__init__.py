@@ -34,7 +34,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
            "gw_tau_to_freq", "gw_screen", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
-           "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning",
+           "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning", "gw_measure_alu",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
            "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_get_params", "gw_mlp_set_params",
            "gw_cpe_features", "gw_cpe_fit_matrix", "gw_cpe_seed", "gw_cpe_iterations"]
@@ -69,6 +69,15 @@ def _grid_struct(grid, keep):
     return _Grid(float(grid.beta), len(keep["tau"]), keep["tau"].ctypes.data_as(dp), len(keep["poles"]),
                  keep["poles"].ctypes.data_as(dp), len(keep["nu"]), keep["nu"].ctypes.data_as(ip),
                  len(keep["w"]), keep["w"].ctypes.data_as(ip), int(grid.ncont))
+
+
+def measure_alu(device=0):
+    """Measured (FP64 TFLOP/s, FP32 TFLOP/s) FMA throughput of `device`'s CUDA cores."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = lib().gw_measure_alu(int(device), ctypes.byref(a), ctypes.byref(b))
+    if st != GW_OK:
+        raise GwError(f"gw_measure_alu: {_STATUS.get(st, st)}")
+    return a.value, b.value
 
 
 def transform_matrices(grid):
@@ -114,6 +123,7 @@ def load_library(path=LIB_PATH):
         "gw_kernel_timing": [vp, i32],
         "gw_set_stream": [vp, vp],
         "gw_set_tuning": [vp, i32, i64],
+        "gw_measure_alu": [i32, vp, vp],
         "gw_kernel_time": [vp, ctypes.c_char_p, vp, vp],
         "gw_screen_static": [i32, i32, i32, vp, vp, vp, vp, vp],
         "gw_mlp_create": [ctypes.POINTER(vp), i32, i32, i32, i32, ctypes.c_uint64, i32, vp],

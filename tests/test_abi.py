@@ -76,3 +76,4 @@ def test_invalid_arguments_rejected_on_host(gw):
     assert lib.gw_set_stream(None, None) == gw.GW_EINVAL
     assert lib.gw_set_tuning(None, gw.GW_TUNE_POL_SEG_CHUNKS, 16) == gw.GW_EINVAL
     assert lib.gw_kernel_timing(None, 1) == gw.GW_EINVAL
+    assert lib.gw_measure_alu(0, None, None) == gw.GW_EINVAL

@@ -426,3 +426,12 @@ def test_c2_full_size_sampled(gw):
     Sg = host(S)
     for k in ks:
         assert rel(Sg[k][:, its], Sr[k][:, its]) < TOL
+
+
+def test_measured_alu_rates(gw):
+    """The CUDA-core rates behind the float-float design: a float-float complex multiply-add (48
+    FP32-pipe operations) must come cheaper than an FP64 one (4 FP64 FMAs)."""
+    fp64, fp32 = gw.measure_alu(0)
+    print(f"FP64 {fp64:.2f} TFLOP/s, FP32 {fp32:.1f} TFLOP/s")
+    assert fp64 > 0.1
+    assert fp32 / 96.0 > fp64 / 8.0  # complex MAC rates: float-float vs native FP64
