@@ -190,28 +190,42 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
     }
     __syncthreads();
     if (bad) break;
-    // rows R: A_Rc <- A_RR^-1 A_Rc for every column block c != R, A_RR <- A_RR^-1
-    for (int c0 = 0; c0 < ni; c0 += GJ_B) {
-      const bool isR = c0 == k0;
-      for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
-        const int r = e / GJ_B, c = e % GJ_B;
-        S u;
-        if (isR) {
-          u = Pinv[r * (GJ_B + 1) + c];
-        } else {
-          Acc a = AR::azero();
-          for (int j = 0; j < GJ_B; ++j) AR::mac(a, Pinv[r * (GJ_B + 1) + j], A[(size_t)(k0 + j) * ni + c0 + c]);
-          u = AR::val(a);
+    // rows R: A_Rc <- A_RR^-1 A_Rc for every column block c != R, A_RR <- A_RR^-1; 256 columns
+    // per pass, register-tiled: thread t computes rows 8 (t & 3) .. + 7 and columns 4 (t >> 2) .. + 3
+    // of the pass, reading the old rows R from A; all reads of a pass finish before its writes
+    for (int cp = 0; cp < ni; cp += 256) {
+      const int rg = t & 3, col = cp + 4 * (t >> 2);
+      const bool live = col < ni;
+      Acc acc[8][4];
+#pragma unroll
+      for (int m = 0; m < 8; ++m)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[m][q] = AR::azero();
+      if (live) {
+        for (int j = 0; j < GJ_B; ++j) {
+          S aq[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) aq[q] = A[(size_t)(k0 + j) * ni + col + q];
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const S pv = Pinv[(8 * rg + m) * (GJ_B + 1) + j];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) AR::mac(acc[m][q], pv, aq[q]);
+          }
         }
-        U[r * (GJ_B + 1) + c] = u;
       }
       __syncthreads();
-      for (int e = t; e < GJ_B * GJ_B; e += blockDim.x) {
-        const int r = e / GJ_B, c = e % GJ_B;
-        A[(size_t)(k0 + r) * ni + c0 + c] = U[r * (GJ_B + 1) + c];
+      if (live) {
+        const bool isR = col >= k0 && col < k0 + GJ_B;  // a 4-column group lies in one 32-block
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            A[(size_t)(k0 + 8 * rg + m) * ni + col + q] =
+                isR ? Pinv[(8 * rg + m) * (GJ_B + 1) + col + q - k0] : AR::val(acc[m][q]);
       }
-      __syncthreads();
     }
+    __syncthreads();
     // all other rows, in passes of GJ_RP rows: A_ic -= A_iR U_c with U_c the new row block
     // (A_iR <- -A_iR A_RR^-1 for the column block R, which starts from zero); the pass's
     // A_iR are taken into shared memory before its column block R is overwritten
