@@ -15,6 +15,8 @@ loops (test infrastructure; see the package docstring).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 import scipy.optimize as _so
 
@@ -107,8 +109,8 @@ def cpe_resig(b, x):
 
 
 # ---------------------------------------------------------------- QP
-QP_SCAN = 401        # scan points on [eps - 1, eps + 1] Ha
-QP_STEP = 0.005      # Ha
+QP_STEP = 0.005      # Ha: the scan visits the energies j * QP_STEP within eps +- QP_RANGE
+QP_RANGE = 1.0       # Ha
 QP_BISECT = 60
 
 
@@ -116,16 +118,19 @@ def qp_solve(eps, sigx, vxc, resig, de=1e-6, tol=1e-12, maxit=100):
     """Quasiparticle energy: root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E) nearest eps
     (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where F vanishes).
 
-    F is scanned on E_j = eps + (j - 200) 0.005 Ha, j = 0..400; among the upward crossings
-    F_j < 0 <= F_{j+1} (quasiparticle weight Z > 0) the one whose midpoint is nearest eps is
-    refined by 60 bisections. Without a crossing, Newton iteration from eps (central-difference
+    F is scanned on the fixed energy grid E_j = j 0.005 Ha, for the integers j with
+    eps - 1 <= E_j <= eps + 1 Ha (j from ceil((eps - 1) / 0.005) to floor((eps + 1) / 0.005));
+    among the upward crossings F_j < 0 <= F_{j+1} (quasiparticle weight Z > 0) the one whose
+    midpoint is nearest eps is refined by 60 bisections. Without a crossing, Newton iteration from eps (central-difference
     derivative, steps clamped to 0.5 Ha) is the fallback. Returns (E, Z, ok) with ok False for
     the fallback or a Newton failure."""
     F = lambda E: E - eps - sigx + vxc - resig(E)  # noqa: E731
-    Es = [eps + (j - (QP_SCAN // 2)) * QP_STEP for j in range(QP_SCAN)]
+    j0 = math.ceil((eps - QP_RANGE) / QP_STEP)
+    j1 = math.floor((eps + QP_RANGE) / QP_STEP)
+    Es = [j * QP_STEP for j in range(j0, j1 + 1)]
     Fs = [F(E) for E in Es]
     best = None
-    for j in range(QP_SCAN - 1):
+    for j in range(len(Es) - 1):
         if Fs[j] < 0.0 <= Fs[j + 1]:
             d = abs(0.5 * (Es[j] + Es[j + 1]) - eps)
             if best is None or d < best[0]:

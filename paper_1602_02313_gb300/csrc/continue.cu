@@ -5,7 +5,8 @@
 //          Phi_m(z) = int hat_m(x) / (z - x) dx; b from Lawson-Hanson NNLS on the normal
 //          equations of the ridge-regularised fit (one warp per problem).
 //  * QP  : root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E + i eta), eta = 1e-4 Ha: the
-//          upward crossing nearest eps on a 0.005 Ha scan of eps +- 1 Ha, refined by bisection.
+//          upward crossing nearest eps on the fixed grid j 0.005 Ha within eps +- 1 Ha, refined
+//          by bisection.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -54,32 +55,39 @@ __device__ cd cpe_phi(const double* x, int m, cd z) {
 __device__ double resig_pade(const cd* a, int n, double beta, double E) { return pade_eval(a, n, beta, {E, kEta}).x; }
 
 // QP root nearest eps with an upward crossing of F(E) = E - eps - sx + vxc - Re Sigma^c(E):
-// scan E_j = eps + (j - 200) 0.005 Ha (j = 0..400), refine the crossing nearest eps by 60
-// bisections; without a crossing fall back to Newton from eps (ok = 0).
-constexpr int kQpScan = 401;
+// scan the fixed energy grid E_j = j 0.005 Ha for eps - 1 <= E_j <= eps + 1, refine the
+// crossing nearest eps by 60 bisections; without a crossing fall back to Newton from eps (ok = 0).
 constexpr double kQpStep = 0.005;
+constexpr double kQpRange = 1.0;
+constexpr int kQpMaxScan = 401;  // points of the scan at most: 2 kQpRange / kQpStep + 1
+
+__device__ __forceinline__ int qp_j0(double eps) { return (int)ceil((eps - kQpRange) / kQpStep); }
+__device__ __forceinline__ int qp_j1(double eps) { return (int)floor((eps + kQpRange) / kQpStep); }
 
 template <class F>
 __device__ void qp_solve(F resig, double eps, double sx, double vxc, double* E_out, int* ok_out) {
   auto Ff = [&](double E) { return E - eps - sx + vxc - resig(E); };
-  int best = -1;
+  const int j0 = qp_j0(eps), j1 = qp_j1(eps);
+  bool found = false;
+  int best = 0;
   double bestd = 0.0;
-  double Fprev = Ff(eps - (kQpScan / 2) * kQpStep);
-  for (int j = 0; j < kQpScan - 1; ++j) {
-    const double E1 = eps + (j + 1 - kQpScan / 2) * kQpStep;
+  double Fprev = Ff(j0 * kQpStep);
+  for (int j = j0; j < j1; ++j) {
+    const double E1 = (j + 1) * kQpStep;
     const double F1 = Ff(E1);
     if (Fprev < 0.0 && F1 >= 0.0) {
-      const double E0 = eps + (j - kQpScan / 2) * kQpStep;
+      const double E0 = j * kQpStep;
       const double d = fabs(0.5 * (E0 + E1) - eps);
-      if (best < 0 || d < bestd) {
+      if (!found || d < bestd) {
+        found = true;
         best = j;
         bestd = d;
       }
     }
     Fprev = F1;
   }
-  if (best >= 0) {
-    double lo = eps + (best - kQpScan / 2) * kQpStep, hi = eps + (best + 1 - kQpScan / 2) * kQpStep;
+  if (found) {
+    double lo = best * kQpStep, hi = (best + 1) * kQpStep;
     for (int it = 0; it < 60; ++it) {
       const double mid = 0.5 * (lo + hi);
       if (Ff(mid) < 0.0)
@@ -522,8 +530,26 @@ __device__ double resig_cpe_warp(const double* b, const double* x, int ng, doubl
   return warp_sum(s);
 }
 
+// Re Phi_m(E_j + i eta) of every hat m on the scan grid E_j = j kQpStep, j in
+// [kTabJ0, kTabJ0 + kTabN), with the same arithmetic as resig_cpe_lane (node logarithms from
+// clog_, rise + fall), so that the QP scan from the table gives the same F_j bit for bit.
+constexpr int kTabJ0 = -600, kTabN = 1201;  // E in [-3, 3] Ha
+
+__global__ void k_cpe_table(const double* __restrict__ x, int ng, double* __restrict__ tab) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kTabN * ng) return;
+  const int m = e % ng, jj = e / ng;
+  const cd z = {(kTabJ0 + jj) * kQpStep, kEta};
+  const cd l0 = clog_(csub(z, cd{x[m], 0.0})), l1 = clog_(csub(z, cd{x[m + 1], 0.0})),
+           l2 = clog_(csub(z, cd{x[m + 2], 0.0}));
+  const double x0 = x[m], x1 = x[m + 1], x2 = x[m + 2];
+  const cd rise = csub(cmul(cd{(z.x - x0) / (x1 - x0), z.y / (x1 - x0)}, csub(l0, l1)), cd{1.0, 0.0});
+  const cd fall = cadd(cmul(cd{(x2 - z.x) / (x2 - x1), -z.y / (x2 - x1)}, csub(l1, l2)), cd{1.0, 0.0});
+  tab[e] = rise.x + fall.x;
+}
+
 __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const double* __restrict__ x, int ng,
-                         const double* __restrict__ eps, const double* __restrict__ sigx,
+                         const double* __restrict__ tab, const double* __restrict__ eps, const double* __restrict__ sigx,
                          const double* __restrict__ vxc, int nreal, const double* __restrict__ wr,
                          double2* __restrict__ sreal, double* __restrict__ eqp, int* __restrict__ info) {
   const int64_t p = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -544,24 +570,36 @@ __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const doub
   }
   const double e0 = eps[p], s0 = sigx[p], v0 = vxc[p];
   auto F = [&](double E) { return E - e0 - s0 + v0 - resig_cpe_warp(bp, x, ng, E, lane); };
-  // scan: F at E_j = e0 + (j - 200) kQpStep, j = 0 .. 400; lanes take consecutive blocks
-  constexpr int per = (kQpScan + 31) / 32;  // 13 points per lane
-  double fv[per + 1];
+  // scan: F at E_j = j kQpStep, j0 <= j <= j1, lanes take consecutive blocks. Inside the range of
+  // the table (each hat's Re Phi_m on the grid, built by gw_cpe_setup with the same arithmetic as
+  // resig_cpe_lane) Re Sigma^c(E_j) is a dot product over the active hats; outside it each lane
+  // evaluates the hats itself.
+  const int j0 = qp_j0(e0), j1 = qp_j1(e0), nscan = j1 - j0 + 1;
+  const int per = (nscan + 31) / 32;
+  const bool use_tab = tab != nullptr && j0 >= kTabJ0 && j1 < kTabJ0 + kTabN;
+  double fv[kQpMaxScan / 32 + 2];
   for (int q = 0; q <= per; ++q) {
-    const int j = lane * per + q;
-    const int jj = j < kQpScan ? j : kQpScan - 1;
-    const double E = e0 + (jj - kQpScan / 2) * kQpStep;
-    fv[q] = E - e0 - s0 + v0 - resig_cpe_lane(bp, x, ng, E);
+    const int i = min(lane * per + q, nscan - 1);
+    const double E = (j0 + i) * kQpStep;
+    double rs = 0.0;
+    if (use_tab) {
+      const double* T = tab + (size_t)(j0 + i - kTabJ0) * ng;
+      for (int m = 0; m < ng; ++m)
+        if (bp[m] != 0.0) rs += bp[m] * T[m];
+    } else {
+      rs = resig_cpe_lane(bp, x, ng, E);
+    }
+    fv[q] = E - e0 - s0 + v0 - rs;
   }
   int best = -1;
   double bestd = 0.0;
   for (int q = 0; q < per; ++q) {
-    const int j = lane * per + q;
-    if (j + 1 >= kQpScan) break;
+    const int i = lane * per + q;
+    if (i + 1 >= nscan) break;
     if (fv[q] < 0.0 && fv[q + 1] >= 0.0) {
-      const double d = fabs(0.5 * ((e0 + (j - kQpScan / 2) * kQpStep) + (e0 + (j + 1 - kQpScan / 2) * kQpStep)) - e0);
-      if (best < 0 || d < bestd || (d == bestd && j < best)) {
-        best = j;
+      const double d = fabs(0.5 * ((j0 + i) * kQpStep + (j0 + i + 1) * kQpStep) - e0);
+      if (best < 0 || d < bestd || (d == bestd && i < best)) {
+        best = i;
         bestd = d;
       }
     }
@@ -577,7 +615,7 @@ __global__ void k_cpe_qp(int64_t nprob, const double* __restrict__ b, const doub
   double E;
   int ok;
   if (best >= 0) {
-    double lo = e0 + (best - kQpScan / 2) * kQpStep, hi = e0 + (best + 1 - kQpScan / 2) * kQpStep;
+    double lo = (j0 + best) * kQpStep, hi = (j0 + best + 1) * kQpStep;
     for (int it = 0; it < 60; ++it) {
       const double mid = 0.5 * (lo + hi);
       if (F(mid) < 0.0)
@@ -650,7 +688,8 @@ gw_status launch_continue(gw_ctx* c, int method, int64_t nprob, const double* si
                                                      c->cpe_ngrid, seed, c->d_cpe_b, info, c->d_cpe_iters);
   gw_status s = check_launch(c, "cpe_nnls");
   if (s != GW_OK) return s;
-  k_cpe_qp<<<(unsigned)((nprob + 3) / 4), 128, 0, c->stream>>>(nprob, c->d_cpe_b, c->d_cpe_x, c->cpe_ngrid, eps,
+  k_cpe_qp<<<(unsigned)((nprob + 3) / 4), 128, 0, c->stream>>>(nprob, c->d_cpe_b, c->d_cpe_x, c->cpe_ngrid,
+                                                                 c->d_cpe_tab, eps,
                                                                  sigx, vxc, nreal, omega_real, (double2*)sig_real,
                                                                  e_qp, info);
   return check_launch(c, "cpe_qp");
@@ -685,20 +724,23 @@ extern "C" gw_status gw_cpe_setup(gw_ctx* c, int ng, const double* x, double rid
       for (int r = 0; r < 2 * nc; ++r) s += A[(size_t)r * ng + i] * A[(size_t)r * ng + j];
       N[(size_t)i * ng + j] = s + (i == j ? lam2 : 0.0);
     }
-  for (double** p : {&c->d_cpe_x, &c->d_cpe_A, &c->d_cpe_N})
+  for (double** p : {&c->d_cpe_x, &c->d_cpe_A, &c->d_cpe_N, &c->d_cpe_tab})
     if (*p) {
       cudaFree(*p);
       *p = nullptr;
     }
   if (cudaMalloc((void**)&c->d_cpe_x, sizeof(double) * (ng + 2)) != cudaSuccess ||
       cudaMalloc((void**)&c->d_cpe_A, sizeof(double) * A.size()) != cudaSuccess ||
-      cudaMalloc((void**)&c->d_cpe_N, sizeof(double) * N.size()) != cudaSuccess) {
+      cudaMalloc((void**)&c->d_cpe_N, sizeof(double) * N.size()) != cudaSuccess ||
+      cudaMalloc((void**)&c->d_cpe_tab, sizeof(double) * kTabN * ng) != cudaSuccess) {
     cudaGetLastError();
     return set_err(c, GW_ENOMEM, "gw_cpe_setup");
   }
   cudaMemcpy(c->d_cpe_x, x, sizeof(double) * (ng + 2), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_cpe_A, A.data(), sizeof(double) * A.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_cpe_N, N.data(), sizeof(double) * N.size(), cudaMemcpyHostToDevice);
+  k_cpe_table<<<(kTabN * ng + 255) / 256, 256, 0, c->stream>>>(c->d_cpe_x, ng, c->d_cpe_tab);
+  if (check_launch(c, "cpe_table") != GW_OK) return GW_ECUDA;
   c->cpe_ngrid = ng;
   c->cpe_ridge = ridge;
   c->cpe_x.assign(x, x + ng + 2);

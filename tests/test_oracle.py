@@ -355,7 +355,7 @@ def test_cpe_kernel_asymptote_and_exact_recovery():
 
 
 def test_qp_quadratic_closed_form():
-    eps, sx, vxc, g2, E0 = 0.2, -1.0, -1.1, 0.03, 0.9
+    eps, sx, vxc, g2, E0 = 0.2, -1.0, -1.1, 0.03, 0.9013  # pole off the 0.005 Ha scan grid
     resig = lambda E: g2 / (E - E0)  # noqa: E731
     E, Z, ok = orc.qp_solve(eps, sx, vxc, resig)
     # E - eps - sx + vxc = g2/(E - E0)  ->  quadratic, root nearest eps
