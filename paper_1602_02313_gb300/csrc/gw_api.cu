@@ -221,9 +221,46 @@ gw_status launch_dyson(gw_ctx* c, const double* eps, const double* sigx, const d
 // ----------------------------------------------------------------------------
 // BOSE tau -> i nu: out[j][b] = sum_i T[j][i] in[i][b]  (complex T, complex data).
 // The arithmetic is a policy: FP64, or float-float (arith.cuh) on the FP32 pipes.
+// FP64 complex -> float-float, once per transform call.
+__global__ void k_to_ff(const double2* __restrict__ in, arith::Ff32::S* __restrict__ out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = arith::Ff32::from(in[i].x, in[i].y);
+}
+
+// ghat = (W_IJ + W_JI)/2 and hhat = (W_IJ - W_JI)/(2i) of a Hermitian-matrix function in
+// float-float, the same operations as k_bose_bwd's own (one pass over W instead of one per tau block).
+__global__ void k_to_ff_sym(const double2* __restrict__ W, int m, int64_t nf, arith::Ff32::S* __restrict__ G,
+                            arith::Ff32::S* __restrict__ H) {
+  using AR = arith::Ff32;
+  const int64_t mm = (int64_t)m * m;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nf * mm) return;
+  const int64_t j = i / mm, e = i % mm;
+  const int I = (int)(e / m), J = (int)(e % m);
+  const double2 ad = W[i], bd = W[j * mm + (int64_t)J * m + I];
+  const AR::S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
+  G[i] = AR::half(AR::add(a, bv));
+  H[i] = AR::mul_mi(AR::half(AR::dif(a, bv)));
+}
+
+static gw_status grow_ws(gw_ctx* c, size_t need) {
+  if (need <= c->ff_ws_bytes) return GW_OK;
+  if (c->ff_ws) cudaFree(c->ff_ws);
+  c->ff_ws = nullptr;
+  c->ff_ws_bytes = 0;
+  if (cudaMalloc(&c->ff_ws, need) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(c, GW_ENOMEM, "transform workspace");
+  }
+  c->ff_ws_bytes = need;
+  return GW_OK;
+}
+
+// Input values in the policy's storage type (FP64 data as is; float-float data converted once
+// beforehand by k_to_ff, so that the FP64-pipe conversions are not repeated per frequency block).
 template <int JB, class AR>
-__global__ void k_bose_fwd(const double2* __restrict__ T, const double2* __restrict__ in, double2* __restrict__ out,
-                           int64_t batch, int ntau, int nf) {
+__global__ void k_bose_fwd(const double2* __restrict__ T, const typename AR::S* __restrict__ in,
+                           double2* __restrict__ out, int64_t batch, int ntau, int nf) {
   using S = typename AR::S;
   extern __shared__ __align__(16) unsigned char bfsm[];
   S* sT = reinterpret_cast<S*>(bfsm);
@@ -236,8 +273,7 @@ __global__ void k_bose_fwd(const double2* __restrict__ T, const double2* __restr
 #pragma unroll
     for (int q = 0; q < JB; ++q) acc[q] = AR::azero();
     for (int i = 0; i < ntau; ++i) {
-      const double2 xd = in[(size_t)i * batch + b];
-      const S x = AR::from(xd.x, xd.y);
+      const S x = in[(size_t)i * batch + b];
 #pragma unroll
       for (int q = 0; q < JB; ++q)
         if (j0 + q < nf) AR::mac(acc[q], sT[(j0 + q) * ntau + i], x);
@@ -251,9 +287,11 @@ __global__ void k_bose_fwd(const double2* __restrict__ T, const double2* __restr
 // BOSE i nu -> tau of a Hermitian-matrix function W[j][I][J]:
 // ghat = (W_IJ + W_JI)/2 (transform of Re W(tau)), hhat = (W_IJ - W_JI)/(2i) (of Im W(tau));
 // Re W(tau_i) = sum_j A_ij Re ghat_j + B_ij Im ghat_j, Im W(tau_i) likewise with hhat.
-template <int IB, class AR>
-__global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W, double2* __restrict__ out,
-                           int m, int ntau, int nf) {
+// PRE: ghat and hhat come precomputed in float-float (k_to_ff_sym) instead of from W.
+template <int IB, class AR, bool PRE>
+__global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W,
+                           const typename AR::S* __restrict__ Gh, const typename AR::S* __restrict__ Hh,
+                           double2* __restrict__ out, int m, int ntau, int nf) {
   using S = typename AR::S;
   using R = typename AR::R;
   extern __shared__ __align__(16) unsigned char bbsm[];
@@ -270,10 +308,16 @@ __global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restr
 #pragma unroll
     for (int q = 0; q < IB; ++q) acc[q] = AR::azero();
     for (int j = 0; j < nf; ++j) {
-      const double2 ad = W[(size_t)j * mm + e], bd = W[(size_t)j * mm + et];
-      const S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
-      const S g = AR::half(AR::add(a, bv));
-      const S h = AR::mul_mi(AR::half(AR::dif(a, bv)));
+      S g, h;
+      if (PRE) {
+        g = Gh[(size_t)j * mm + e];
+        h = Hh[(size_t)j * mm + e];
+      } else {
+        const double2 ad = W[(size_t)j * mm + e], bd = W[(size_t)j * mm + et];
+        const S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
+        g = AR::half(AR::add(a, bv));
+        h = AR::mul_mi(AR::half(AR::dif(a, bv)));
+      }
 #pragma unroll
       for (int q = 0; q < IB; ++q)
         if (i0 + q < ntau) AR::rmac2(acc[q], sTb[(i0 + q) * 2 * nf + j], sTb[(i0 + q) * 2 * nf + nf + j], g, h);
@@ -325,10 +369,16 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch
   if (stat == GW_BOSE && dir == GW_TAU_TO_IW) {
     const int64_t blocks = (batch + 127) / 128;
     if (prec == GW_F32X2) {
-      const size_t sm = sizeof(arith::Ff32::S) * c->nnu * nt;
+      using S = arith::Ff32::S;
+      const int64_t n = (int64_t)nt * batch;
+      gw_status st;
+      if ((st = grow_ws(c, sizeof(S) * n)) != GW_OK) return st;
+      k_to_ff<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, (S*)c->ff_ws, n);
+      if ((st = check_launch(c, "to_ff")) != GW_OK) return st;
+      const size_t sm = sizeof(S) * c->nnu * nt;
       if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       k_bose_fwd<16, arith::Ff32><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
-                                                                             (const double2*)in, (double2*)out, batch,
+                                                                             (const S*)c->ff_ws, (double2*)out, batch,
                                                                              nt, c->nnu);
     } else {
       const size_t sm = sizeof(double2) * c->nnu * nt;
@@ -344,15 +394,25 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch
     const int64_t mm = (int64_t)m * m;
     const unsigned blocks = (unsigned)((mm + 127) / 128);
     if (prec == GW_F32X2) {
+      using S = arith::Ff32::S;
+      const int64_t n = (int64_t)c->nnu * mm;
+      gw_status st;
+      if ((st = grow_ws(c, 2 * sizeof(S) * n)) != GW_OK) return st;
+      S* Gh = (S*)c->ff_ws;
+      S* Hh = Gh + n;
+      k_to_ff_sym<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, m, c->nnu, Gh, Hh);
+      if ((st = check_launch(c, "to_ff_sym")) != GW_OK) return st;
       const size_t sm = sizeof(arith::Ff32::R) * nt * 2 * c->nnu;
-      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<16, arith::Ff32><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m, nt,
-                                                                   c->nnu);
+      if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_bose_bwd<16, arith::Ff32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_bwd<16, arith::Ff32, true><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, nullptr, Gh, Hh, (double2*)out, m,
+                                                                         nt, c->nnu);
     } else {
       const size_t sm = sizeof(double) * nt * 2 * c->nnu;
-      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<8, arith::Fp64><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, (double2*)out, m, nt,
-                                                                  c->nnu);
+      if (sm > 48 * 1024)
+        cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      k_bose_bwd<8, arith::Fp64, false><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, nullptr,
+                                                                         nullptr, (double2*)out, m, nt, c->nnu);
     }
     return check_launch(c, "bose_bwd");
   }
@@ -590,6 +650,8 @@ gw_status gw_destroy(gw_ctx* c) {
   c->m_done.clear();
   if (c->m_stream) cudaStreamDestroy(c->m_stream);
   c->m_stream = nullptr;
+  if (c->ff_ws) cudaFree(c->ff_ws);
+  c->ff_ws = nullptr;
   double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
                     c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_tab, c->d_cpe_b,
                     c->d_pade,  c->d_vm};

@@ -94,7 +94,9 @@ struct gw_ctx {
   double* d_cpe_x = nullptr;
   double* d_cpe_A = nullptr;    // real [2 ncont][ngrid]
   double* d_cpe_N = nullptr;    // real [ngrid][ngrid]: A^T A + lambda^2 I
-  double* d_cpe_tab = nullptr;  // real [1201][ngrid]: Re Phi_m on the QP scan grid
+  double* d_cpe_tab = nullptr;
+  void* ff_ws = nullptr;        // float-float copies of a bosonic transform's input
+  size_t ff_ws_bytes = 0;  // real [1201][ngrid]: Re Phi_m on the QP scan grid
   double* d_cpe_b = nullptr;    // [nprob][ngrid]
   size_t cpe_b_bytes = 0;
   int64_t cpe_nprob = 0;       // problems of the last GW_CPE call
