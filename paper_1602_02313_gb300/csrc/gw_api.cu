@@ -261,27 +261,30 @@ static gw_status grow_ws(gw_ctx* c, size_t need) {
 template <int JB, class AR>
 __global__ void k_bose_fwd(const double2* __restrict__ T, const typename AR::S* __restrict__ in,
                            double2* __restrict__ out, int64_t batch, int ntau, int nf) {
+  // block (x, y): 128 batch elements x frequencies j0 .. j0 + JB - 1 (grid.y = ceil(nf / JB))
   using S = typename AR::S;
   extern __shared__ __align__(16) unsigned char bfsm[];
   S* sT = reinterpret_cast<S*>(bfsm);
-  for (int i = threadIdx.x; i < nf * ntau; i += blockDim.x) sT[i] = AR::from(T[i].x, T[i].y);
+  const int j0 = blockIdx.y * JB, nj = min(JB, nf - j0);
+  for (int i = threadIdx.x; i < nj * ntau; i += blockDim.x) {
+    const double2 t = T[(size_t)j0 * ntau + i];
+    sT[i] = AR::from(t.x, t.y);
+  }
   __syncthreads();
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (b >= batch) return;
-  for (int j0 = 0; j0 < nf; j0 += JB) {
-    typename AR::Acc acc[JB];
+  typename AR::Acc acc[JB];
 #pragma unroll
-    for (int q = 0; q < JB; ++q) acc[q] = AR::azero();
-    for (int i = 0; i < ntau; ++i) {
-      const S x = in[(size_t)i * batch + b];
-#pragma unroll
-      for (int q = 0; q < JB; ++q)
-        if (j0 + q < nf) AR::mac(acc[q], sT[(j0 + q) * ntau + i], x);
-    }
+  for (int q = 0; q < JB; ++q) acc[q] = AR::azero();
+  for (int i = 0; i < ntau; ++i) {
+    const S x = in[(size_t)i * batch + b];
 #pragma unroll
     for (int q = 0; q < JB; ++q)
-      if (j0 + q < nf) out[(size_t)(j0 + q) * batch + b] = AR::to(AR::val(acc[q]));
+      if (q < nj) AR::mac(acc[q], sT[q * ntau + i], x);
   }
+#pragma unroll
+  for (int q = 0; q < JB; ++q)
+    if (q < nj) out[(size_t)(j0 + q) * batch + b] = AR::to(AR::val(acc[q]));
 }
 
 // BOSE i nu -> tau of a Hermitian-matrix function W[j][I][J]:
@@ -292,40 +295,40 @@ template <int IB, class AR, bool PRE>
 __global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W,
                            const typename AR::S* __restrict__ Gh, const typename AR::S* __restrict__ Hh,
                            double2* __restrict__ out, int m, int ntau, int nf) {
+  // block (x, y): 128 matrix elements x tau points i0 .. i0 + IB - 1 (grid.y = ceil(ntau / IB))
   using S = typename AR::S;
   using R = typename AR::R;
   extern __shared__ __align__(16) unsigned char bbsm[];
   R* sTb = reinterpret_cast<R*>(bbsm);
-  for (int i = threadIdx.x; i < ntau * 2 * nf; i += blockDim.x) sTb[i] = AR::rfrom(Tb[i]);
+  const int i0 = blockIdx.y * IB, ni = min(IB, ntau - i0);
+  for (int i = threadIdx.x; i < ni * 2 * nf; i += blockDim.x) sTb[i] = AR::rfrom(Tb[(size_t)i0 * 2 * nf + i]);
   __syncthreads();
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t mm = (int64_t)m * m;
   if (e >= mm) return;
   const int I = (int)(e / m), J = (int)(e % m);
   const int64_t et = (int64_t)J * m + I;
-  for (int i0 = 0; i0 < ntau; i0 += IB) {
-    typename AR::Acc acc[IB];  // re: Re W(tau), im: Im W(tau)
+  typename AR::Acc acc[IB];  // re: Re W(tau), im: Im W(tau)
 #pragma unroll
-    for (int q = 0; q < IB; ++q) acc[q] = AR::azero();
-    for (int j = 0; j < nf; ++j) {
-      S g, h;
-      if (PRE) {
-        g = Gh[(size_t)j * mm + e];
-        h = Hh[(size_t)j * mm + e];
-      } else {
-        const double2 ad = W[(size_t)j * mm + e], bd = W[(size_t)j * mm + et];
-        const S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
-        g = AR::half(AR::add(a, bv));
-        h = AR::mul_mi(AR::half(AR::dif(a, bv)));
-      }
-#pragma unroll
-      for (int q = 0; q < IB; ++q)
-        if (i0 + q < ntau) AR::rmac2(acc[q], sTb[(i0 + q) * 2 * nf + j], sTb[(i0 + q) * 2 * nf + nf + j], g, h);
+  for (int q = 0; q < IB; ++q) acc[q] = AR::azero();
+  for (int j = 0; j < nf; ++j) {
+    S g, h;
+    if (PRE) {
+      g = Gh[(size_t)j * mm + e];
+      h = Hh[(size_t)j * mm + e];
+    } else {
+      const double2 ad = W[(size_t)j * mm + e], bd = W[(size_t)j * mm + et];
+      const S a = AR::from(ad.x, ad.y), bv = AR::from(bd.x, bd.y);
+      g = AR::half(AR::add(a, bv));
+      h = AR::mul_mi(AR::half(AR::dif(a, bv)));
     }
 #pragma unroll
     for (int q = 0; q < IB; ++q)
-      if (i0 + q < ntau) out[(size_t)(i0 + q) * mm + e] = AR::to(AR::val(acc[q]));
+      if (q < ni) AR::rmac2(acc[q], sTb[q * 2 * nf + j], sTb[q * 2 * nf + nf + j], g, h);
   }
+#pragma unroll
+  for (int q = 0; q < IB; ++q)
+    if (q < ni) out[(size_t)(i0 + q) * mm + e] = AR::to(AR::val(acc[q]));
 }
 
 // FERMI tau -> i w of real rows: out[b][j] = sum_i T[j][i] in[b][i]; one thread per (b, j).
@@ -375,15 +378,15 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch
       if ((st = grow_ws(c, sizeof(S) * n)) != GW_OK) return st;
       k_to_ff<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, (S*)c->ff_ws, n);
       if ((st = check_launch(c, "to_ff")) != GW_OK) return st;
-      const size_t sm = sizeof(S) * c->nnu * nt;
+      const size_t sm = sizeof(S) * 16 * nt;
       if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_fwd<16, arith::Ff32><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
+      k_bose_fwd<16, arith::Ff32><<<dim3((unsigned)blocks, (c->nnu + 15) / 16), 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
                                                                              (const S*)c->ff_ws, (double2*)out, batch,
                                                                              nt, c->nnu);
     } else {
-      const size_t sm = sizeof(double2) * c->nnu * nt;
+      const size_t sm = sizeof(double2) * 8 * nt;
       if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_fwd<8, arith::Fp64><<<(unsigned)blocks, 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
+      k_bose_fwd<8, arith::Fp64><<<dim3((unsigned)blocks, (c->nnu + 7) / 8), 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
                                                                             (const double2*)in, (double2*)out, batch,
                                                                             nt, c->nnu);
     }
@@ -402,16 +405,16 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch
       S* Hh = Gh + n;
       k_to_ff_sym<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, m, c->nnu, Gh, Hh);
       if ((st = check_launch(c, "to_ff_sym")) != GW_OK) return st;
-      const size_t sm = sizeof(arith::Ff32::R) * nt * 2 * c->nnu;
+      const size_t sm = sizeof(arith::Ff32::R) * 16 * 2 * c->nnu;
       if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_bose_bwd<16, arith::Ff32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<16, arith::Ff32, true><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, nullptr, Gh, Hh, (double2*)out, m,
+      k_bose_bwd<16, arith::Ff32, true><<<dim3(blocks, (nt + 15) / 16), 128, sm, c->stream>>>(c->d_Bbwd, nullptr, Gh, Hh, (double2*)out, m,
                                                                          nt, c->nnu);
     } else {
-      const size_t sm = sizeof(double) * nt * 2 * c->nnu;
+      const size_t sm = sizeof(double) * 8 * 2 * c->nnu;
       if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<8, arith::Fp64, false><<<blocks, 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, nullptr,
+      k_bose_bwd<8, arith::Fp64, false><<<dim3(blocks, (nt + 7) / 8), 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, nullptr,
                                                                          nullptr, (double2*)out, m, nt, c->nnu);
     }
     return check_launch(c, "bose_bwd");
@@ -446,12 +449,21 @@ __global__ void k_vm(const double2* __restrict__ M, const double* __restrict__ v
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const double2* Mk = M + (size_t)k * ni * np + p;
-  double s = 0.0;
-  for (int I = 0; I < ni; ++I) {
-    const double2 m = Mk[(size_t)I * np];
-    s = fma(v[I], fma(m.x, m.x, m.y * m.y), s);
+  // 8 loads in flight per thread, one partial sum per residue of I mod 8
+  double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  int I = 0;
+  for (; I + 8 <= ni; I += 8) {
+    double2 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Mk[(size_t)(I + u) * np];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] = fma(v[I + u], fma(m[u].x, m[u].x, m[u].y * m[u].y), s[u]);
   }
-  vm[(size_t)k * np + p] = s;
+  for (; I < ni; ++I) {
+    const double2 m = Mk[(size_t)I * np];
+    s[0] = fma(v[I], fma(m.x, m.x, m.y * m.y), s[0]);
+  }
+  vm[(size_t)k * np + p] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
 __global__ void k_sigx_occ(const double* __restrict__ vm, const int* __restrict__ kmq, const double* __restrict__ occ,

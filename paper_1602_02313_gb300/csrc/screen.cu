@@ -191,8 +191,10 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
     __syncthreads();
     if (bad) break;
     // rows R: A_Rc <- A_RR^-1 A_Rc for every column block c != R, A_RR <- A_RR^-1; 256 columns
-    // per pass, register-tiled: thread t computes rows 8 (t & 3) .. + 7 and columns 4 (t >> 2) .. + 3
-    // of the pass, reading the old rows R from A; all reads of a pass finish before its writes
+    // per pass, register-tiled: thread t computes rows (t & 3) + 4 m, m = 0 .. 7 (interleaved, so
+    // that the four row groups of a warp read Pinv from four different bank groups) and columns
+    // 4 (t >> 2) .. + 3 of the pass, reading the old rows R from A; all reads of a pass finish
+    // before its writes
     for (int cp = 0; cp < ni; cp += 256) {
       const int rg = t & 3, col = cp + 4 * (t >> 2);
       const bool live = col < ni;
@@ -208,7 +210,7 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
           for (int q = 0; q < 4; ++q) aq[q] = A[(size_t)(k0 + j) * ni + col + q];
 #pragma unroll
           for (int m = 0; m < 8; ++m) {
-            const S pv = Pinv[(8 * rg + m) * (GJ_B + 1) + j];
+            const S pv = Pinv[(rg + 4 * m) * (GJ_B + 1) + j];
 #pragma unroll
             for (int q = 0; q < 4; ++q) AR::mac(acc[m][q], pv, aq[q]);
           }
@@ -221,8 +223,8 @@ __global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict
         for (int m = 0; m < 8; ++m)
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            A[(size_t)(k0 + 8 * rg + m) * ni + col + q] =
-                isR ? Pinv[(8 * rg + m) * (GJ_B + 1) + col + q - k0] : AR::val(acc[m][q]);
+            A[(size_t)(k0 + rg + 4 * m) * ni + col + q] =
+                isR ? Pinv[(rg + 4 * m) * (GJ_B + 1) + col + q - k0] : AR::val(acc[m][q]);
       }
     }
     __syncthreads();

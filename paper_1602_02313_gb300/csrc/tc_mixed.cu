@@ -380,44 +380,56 @@ __device__ __forceinline__ size_t xs_tile(int k, int pblk, int kc, int sl, int n
   return ((((size_t)k * npb + pblk) * nkc + kc) * 4 + sl) * (size_t)(128 * 32);  // in halves
 }
 
-// Split M[q] into XS via a 32 x 32 shared-memory transpose (rows p >= nb^2 zero), and
-// write the epilogue's image XE[k][pblk][I][row] = 2^8 M (FP32 re, im; rows contiguous, so
-// that the 32 lanes of a warp, which own 32 consecutive rows, read 256 contiguous bytes).
-__global__ void k_split_x(const double2* __restrict__ Mq, int ni, int np, int npb, __half* __restrict__ XS,
-                          float2* __restrict__ XE) {
-  __shared__ double2 tileS[32][33];
+// Split M[q] into XS and write the epilogue's image XE[k][pblk][I][row] = 2^8 M (FP32 re, im;
+// rows contiguous, so that the 32 lanes of a warp, which own 32 consecutive rows, read 256
+// contiguous bytes). One block per (k, 32 pairs, 64 I): each thread issues its 8 loads before
+// the first use; the scaled FP32 values go through a 64 x 32 shared-memory transpose (rows
+// I, padded to 33, columns XOR-swizzled by 2 ((I >> 4) & 3) so that both the row-wise writes
+// and the column-wise reads below are free of bank conflicts) and are split into the fp16
+// hi / lo slices of XS (rows p >= nb^2 zero).
+constexpr int SX_I = 64;
+__global__ void __launch_bounds__(256) k_split_x(const double2* __restrict__ Mq, int ni, int np, int npb,
+                                                 __half* __restrict__ XS, float2* __restrict__ XE) {
+  __shared__ float2 tileF[SX_I][33];
   const int k = blockIdx.z;
-  const int p0 = blockIdx.x * 32, I0 = blockIdx.y * 32;
+  const int p0 = blockIdx.x * 32, I0 = blockIdx.y * SX_I;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    const int I = I0 + r, p = p0 + tx;
-    const double2 v = (I < ni && p < np) ? Mq[((size_t)k * ni + I) * np + p] : make_double2(0.0, 0.0);
-    tileS[r][tx] = v;
-    if (I < ni)
-      XE[(((size_t)k * npb + (p >> 7)) * ni + I) * 128 + (p & 127)] =
-          make_float2((float)(v.x * kScaleA), (float)(v.y * kScaleA));
+  const int p = p0 + tx;
+  double2 v[SX_I / 8];
+#pragma unroll
+  for (int j = 0; j < SX_I / 8; ++j) {
+    const int I = I0 + ty + 8 * j;
+    v[j] = (I < ni && p < np) ? Mq[((size_t)k * ni + I) * np + p] : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int j = 0; j < SX_I / 8; ++j) {
+    const int r = ty + 8 * j, I = I0 + r;
+    const float2 f = make_float2((float)(v[j].x * kScaleA), (float)(v[j].y * kScaleA));
+    tileF[r][tx ^ (2 * ((r >> 4) & 3))] = f;
+    if (I < ni) XE[(((size_t)k * npb + (p >> 7)) * ni + I) * 128 + (p & 127)] = f;
   }
   __syncthreads();
-  // 128 threads write the 32 rows x 4 groups of 8 columns as 16-byte vectors per slice
+  // thread t: pair row r = t >> 3, group G = t & 7 of 8 consecutive I (K chunk G >> 2, quarter G & 3)
   const int t = ty * 32 + tx;
-  if (t < 128) {
-    const int nkc = ni / 32;
-    const int r = t >> 2, g = t & 3;
-    const int p = p0 + r, I = I0 + 8 * g;
-    h8 rh, rl, ih, il;
+  const int r = t >> 3, G = t & 7;
+  const int Ib = I0 + 8 * G;
+  if (Ib >= ni) return;
+  const int nkc = ni / 32;
+  h8 rh, rl, ih, il;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const double2 v = tileS[8 * g + e][r];
-      split2((float)v.x * kScaleA, rh.v[e], rl.v[e]);
-      split2((float)v.y * kScaleA, ih.v[e], il.v[e]);
-    }
-    const int pblk = p >> 7, row = p & 127, kc = I >> 5;
-    const size_t o = sw64_off(row, I & 31) / 2;
-    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 0, npb, nkc) + o) = rh;
-    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 1, npb, nkc) + o) = rl;
-    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 2, npb, nkc) + o) = ih;
-    *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 3, npb, nkc) + o) = il;
+  for (int e = 0; e < 8; ++e) {
+    const int R = 8 * G + e;
+    const float2 f = tileF[R][r ^ (2 * ((R >> 4) & 3))];
+    split2(f.x, rh.v[e], rl.v[e]);
+    split2(f.y, ih.v[e], il.v[e]);
   }
+  const int pp = p0 + r;
+  const int pblk = pp >> 7, row = pp & 127, kc = Ib >> 5;
+  const size_t o = sw64_off(row, Ib & 31) / 2;
+  *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 0, npb, nkc) + o) = rh;
+  *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 1, npb, nkc) + o) = rl;
+  *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 2, npb, nkc) + o) = ih;
+  *reinterpret_cast<h8*>(XS + xs_tile(k, pblk, kc, 3, npb, nkc) + o) = il;
 }
 
 // Split W~(tau) into WS: image row R, K column C holds U[C][R] and V[C][R]; for C < R these
@@ -767,7 +779,7 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   if (c->mw.iq != iq || c->mw.prec != prec) {
     const double2* Mq = (const double2*)m_block(c, iq);
     if (!Mq) return GW_ECUDA;
-    dim3 g(npp / 32, (c->ni + 31) / 32, c->nk);
+    dim3 g(npp / 32, (c->ni + SX_I - 1) / SX_I, c->nk);
     k_split_x<<<g, dim3(32, 8), 0, c->stream>>>(Mq, c->ni, np, npb, XS, XE);
     if ((st = check_launch(c, "split_x")) != GW_OK) return st;
     c->mw.iq = iq;
