@@ -172,6 +172,7 @@ def _config(cfg, args, prec):
     return {"workload": f"synthetic crystal {cfg}: Nk={c['nk']} (q on the same grid), Nb={c['nb']} "
                         f"({c['nocc']} occ), NI={c['ni']}, Ntau={c['ntau']}, Nnu=Nw={c['nnu']}, beta={c['beta']}",
             "precision": prec, "omega": args.omega, "continuation": getattr(args, "cont", "pade"),
+            "screening": getattr(args, "screen", "f32") if prec != "fp64" else "fp64",
             "parallelism": f"q-split over {args.gpus} GPU(s)",
             "l2": "inputs larger than L2 (M tensor %.1f GB per q, P(tau) and W~(tau) %.0f MB per q each)" % (
                 c["nk"] * c["ni"] * c["nb"] ** 2 * 16 / 1e9, c["ntau"] * c["ni"] ** 2 * 16 / 1e6)}
@@ -218,6 +219,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gw", choices=["gw", "reference"])
     ap.add_argument("--prec", default="fp16x2", choices=["fp16x2", "fp64"])
+    ap.add_argument("--screen", default="f32", choices=["f32", "f32x2"],
+                    help="arithmetic of the dielectric solve on the mixed chain (float-float or FP32)")
     ap.add_argument("--config", default="nk64_nb64")
     ap.add_argument("--omega", type=float, default=None,
                     help="unit-cell volume in 1/(Omega Nk); default: the paper's Si cell, 270.1 bohr^3")
@@ -269,7 +272,9 @@ def main():
         mlp, mlp_hist = learned.trained_seed(args.omega, device=local)
     ctx = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)
     eps = torch.from_numpy(cr.eps).cuda()
-    chain = Chain(ctx, eps, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
+    sprec = None if prec == gw.GW_FP64 else {"f32x2": gw.GW_F32X2, "f32": gw.GW_F32}[args.screen]
+    chain = Chain(ctx, eps, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp,
+                  screen_prec=sprec)
     fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, gr.ntau)
     flops_step = (fp + fs) * nq
 
@@ -346,18 +351,21 @@ def main():
         kname = dom
         achieved = per_launch_flops[dom] / (kt[dom] * 1e-3) / 1e12 if dom in kt else None
         label = "gw_" + dom + " (whole call)"
-    # the float-float screening against the measured float-float rate of the FP32 pipes:
-    # NI^3 complex multiply-adds per (q, nu) system (in-place Gauss-Jordan inverse)
+    # the screening against the measured rate of the FP32 pipes: NI^3 complex multiply-adds per
+    # (q, nu) system (in-place Gauss-Jordan inverse); a float-float complex multiply-add is 48
+    # FP32-pipe operations, an FP32 one 4 FMAs
     roof_alu = None
     if "k_screen_inv" in kern and prec != gw.GW_FP64:
         fp64_tf, fp32_tf = gw.measure_alu(local)
         macs = float(cr.ni) ** 3 * len(chain.iqs) * len(gr.nu_idx) * args.steps
         ach = macs / (kern["k_screen_inv"]["total_ms"] * 1e-3) / 1e9
-        peak_ff = fp32_tf * 1e3 / 96.0  # 48 FP32-pipe operations (2 flops each) per complex MAC
-        roof_alu = {"bound": "alu", "kernel": "k_screen_inv<float-float> (CUDA events around each launch)",
-                    "achieved": ach, "peak": peak_ff, "unit": "G complex float-float MAC/s", "frac": ach / peak_ff,
-                    "peak_source": "measured FP32 FMA rate of this GPU (gw_measure_alu, this run) / 48 operations "
-                                   "per float-float complex multiply-add",
+        ops = 48.0 if args.screen == "f32x2" else 4.0
+        arith_name = "float-float" if args.screen == "f32x2" else "FP32"
+        peak_ff = fp32_tf * 1e3 / (2.0 * ops)  # 2 flops per FP32-pipe operation
+        roof_alu = {"bound": "alu", "kernel": f"k_screen_inv<{arith_name}> (CUDA events around each launch)",
+                    "achieved": ach, "peak": peak_ff, "unit": f"G complex {arith_name} MAC/s", "frac": ach / peak_ff,
+                    "peak_source": f"measured FP32 FMA rate of this GPU (gw_measure_alu, this run) / {ops:.0f} "
+                                   f"operations per {arith_name} complex multiply-add",
                     "measured_fp64_tflops": fp64_tf, "measured_fp32_tflops": fp32_tf}
     roof = {"bound": "tensor" if prec != gw.GW_FP64 else "alu", "kernel": label,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -382,7 +390,8 @@ def main():
         for _ in range(args.e2e_steps):
             ctx2 = gw.GW(gr, cr, omega=args.omega, device=local, stream=stream, q0=q0)   # M generated from the seed
             eps_d = eps_h.to("cuda", non_blocking=True)
-            ch = Chain(ctx2, eps_d, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp)
+            ch = Chain(ctx2, eps_d, prec=prec, qb=min(max(cnt, 1), 64), iqs=list(range(cnt)), cont_method=cont, mlp=mlp,
+                       screen_prec=sprec)
             ch.start_g0()
             ch.sigma()
             allreduce_sigma(ch.S, ch.Sx)

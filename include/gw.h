@@ -47,7 +47,8 @@ typedef enum {
   GW_FP64 = 0,    /* native FP64 (CUDA cores); the parity path */
   GW_FP16X2 = 1,  /* tcgen05 tensor cores: fp16 hi/lo split operands, 3 products, FP32 TMEM accumulation */
   GW_BF16X3 = 2,  /* tcgen05 tensor cores: bf16 three-slice split, 6 products, FP32 TMEM accumulation */
-  GW_F32X2 = 3    /* float-float on the FP32 pipes: each value hi + lo in two FP32 (~44-bit significand) */
+  GW_F32X2 = 3,   /* float-float on the FP32 pipes: each value hi + lo in two FP32 (~44-bit significand) */
+  GW_F32 = 4      /* plain FP32 on the CUDA cores (gw_screen only) */
 } gw_prec;
 
 typedef enum { GW_BOSE = 0, GW_FERMI = 1 } gw_stat;
@@ -148,8 +149,9 @@ gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, c
  * multiple of 32 (ni <= 320) X = (1 - Pi)^-1 - 1 from a blocked in-place Gauss-Jordan
  * inversion; otherwise by elimination of [1 - Pi | Pi] (GW_FP64 only). No pivoting:
  * 1 - Pi has Hermitian part >= 1.
- * prec: GW_FP64 (native FP64) or GW_F32X2 (float-float arithmetic, the mixed-precision
- * chain's choice; relative error ~1e-12 per element); else GW_EUNSUPPORTED.
+ * prec: GW_FP64 (native FP64), GW_F32X2 (float-float arithmetic; relative error ~1e-12
+ * per element) or GW_F32 (FP32 arithmetic, blocked inversion only; relative error of the
+ * order of sqrt(ni) 6e-8 cond(1 - Pi), ~1e-6 at ni = 256); else GW_EUNSUPPORTED.
  * P_iv, Wt_iv cplx [nqb][nnu][ni][ni]; info out (device) [nqb][nnu]: 0, or j+1 for a
  * zero pivot at elimination step j (that system's output is then undefined).
  * Uses nqb * nnu * ni * 2 ni * 16 bytes of workspace that the context allocates

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgw.so")
 
 GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ESINGULAR, GW_ENOCONV, GW_ETIMEOUT, GW_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-GW_FP64, GW_FP16X2, GW_BF16X3, GW_F32X2 = 0, 1, 2, 3
+GW_FP64, GW_FP16X2, GW_BF16X3, GW_F32X2, GW_F32 = 0, 1, 2, 3, 4
 GW_BOSE, GW_FERMI = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU, GW_TAU_TO_IW_CONT = 0, 1, 2
 GW_PADE, GW_CPE = 0, 1

@@ -1,5 +1,8 @@
 // Complex arithmetic policies shared by the FP64-bound kernels (screening, transforms).
 //  * Fp64 : double2 values, FP64 fused multiply-adds.
+//  * F32  : float2 values, FP32 fused multiply-adds (rounding error ~6e-8 per operation; for
+//           the dielectric inverse of the mixed chain, whose input P already carries the
+//           ~1e-6 error of the fp16-split tensor-core contraction).
 //  * Ff32 : float-float values (hi + lo, two FP32 each, ~44-bit significand). A product
 //           is hi*hi with its exact rounding error from an FMA plus the two cross terms;
 //           it joins the accumulator through an error-free two-sum (Knuth), the errors
@@ -20,6 +23,7 @@ __device__ __forceinline__ double2 cinv_d(double2 a) {
 }
 
 struct Fp64 {
+  static constexpr int kBlocksPerSm = 1;  // occupancy target of the register-tiled screening kernel
   using S = double2;    // stored value (workspace, shared memory)
   using Acc = double2;  // accumulator
   __device__ static S from(double re, double im) { return make_double2(re, im); }
@@ -47,7 +51,29 @@ struct Fp64 {
   }
 };
 
+struct F32 {
+  static constexpr int kBlocksPerSm = 2;
+  using S = float2;
+  using Acc = float2;
+  __device__ static S from(double re, double im) { return make_float2(__double2float_rn(re), __double2float_rn(im)); }
+  __device__ static double2 to(S v) { return make_double2((double)v.x, (double)v.y); }
+  __device__ static S zero() { return make_float2(0.f, 0.f); }
+  __device__ static Acc azero() { return make_float2(0.f, 0.f); }
+  __device__ static bool is_zero(S v) { return v.x == 0.f && v.y == 0.f; }
+  __device__ static void mac(Acc& a, S l, S u) {  // a += l u
+    a.x = fmaf(l.x, u.x, fmaf(-l.y, u.y, a.x));
+    a.y = fmaf(l.x, u.y, fmaf(l.y, u.x, a.y));
+  }
+  __device__ static S val(Acc a) { return a; }
+  __device__ static S sub(S b, Acc a) { return make_float2(b.x - a.x, b.y - a.y); }  // b - a
+  __device__ static S inv(S v) {  // one reciprocal per pivot: in FP64
+    const double2 r = cinv_d(to(v));
+    return from(r.x, r.y);
+  }
+};
+
 struct Ff32 {
+  static constexpr int kBlocksPerSm = 1;
   struct __align__(16) S {
     float rh, rl, ih, il;
   };

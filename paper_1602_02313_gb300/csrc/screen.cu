@@ -122,9 +122,10 @@ constexpr int GJ_RP = 256;  // rows per update pass (the shared-memory panel)
 
 using arith::Fp64;
 using arith::Ff32;
+using arith::F32;
 
 template <class AR>
-__global__ void __launch_bounds__(256, 1) k_screen_inv(const double2* __restrict__ P, const double* __restrict__ sqrtv,
+__global__ void __launch_bounds__(256, AR::kBlocksPerSm) k_screen_inv(const double2* __restrict__ P, const double* __restrict__ sqrtv,
                                                       int nnu, int ni, typename AR::S* __restrict__ work,
                                                       double2* __restrict__ W, int* __restrict__ info) {
   using S = typename AR::S;
@@ -310,7 +311,11 @@ gw_status launch_screen(gw_ctx* c, int iq0, int nqb, int prec, const double* P, 
     if (!blocked) return set_err(c, GW_EUNSUPPORTED, "gw_screen: GW_F32X2 needs ni a multiple of 32");
     return launch_inv<Ff32>(c, iq0, nsys, P, W, info, aug);
   }
-  if (prec != GW_FP64) return set_err(c, GW_EUNSUPPORTED, "gw_screen: precision must be GW_FP64 or GW_F32X2");
+  if (prec == GW_F32) {
+    if (!blocked) return set_err(c, GW_EUNSUPPORTED, "gw_screen: GW_F32 needs ni a multiple of 32");
+    return launch_inv<F32>(c, iq0, nsys, P, W, info, aug);
+  }
+  if (prec != GW_FP64) return set_err(c, GW_EUNSUPPORTED, "gw_screen: precision must be GW_FP64, GW_F32X2 or GW_F32");
   if (blocked) return launch_inv<Fp64>(c, iq0, nsys, P, W, info, aug);
   k_screen<<<nsys, 512, 0, c->stream>>>((const double2*)P, c->d_sqrtv + (size_t)iq0 * c->ni, c->nnu, c->ni,
                                         (double2*)aug, (double2*)W, info);

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import torch
 
-from . import (GW_BOSE, GW_CPE, GW_F32X2, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
+from . import (GW_BOSE, GW_CPE, GW_F32, GW_F32X2, GW_FERMI, GW_FP16X2, GW_FP64, GW_IW_TO_TAU, GW_PADE, GW_TAU_TO_IW,
                GW_TAU_TO_IW_CONT, GwError)
 
 
@@ -45,11 +45,13 @@ class Chain:
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
         self.nnu, self.nw, self.ncont = len(g.nu_idx), len(g.w_idx), g.ncont
         self.prec = prec
-        # the dielectric solve and the bosonic transforms: native FP64 on the FP64 chain,
-        # float-float on the mixed one
+        # the dielectric solve: native FP64 on the FP64 chain, FP32 on the mixed one (its input P
+        # carries the ~1e-6 error of the fp16-split contraction; screen_prec=GW_F32X2 selects
+        # float-float). The bosonic transforms: FP64 on the FP64 chain, float-float on the mixed one.
         if screen_prec is None:
-            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32X2
+            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32
         self.screen_prec = screen_prec
+        self.bose_prec = GW_FP64 if screen_prec == GW_FP64 else GW_F32X2
         self.iqs = list(range(cr.nq)) if iqs is None else list(iqs)
         self.qb = max(1, min(qb, len(self.iqs)))
         self.cont_method = cont_method
@@ -118,11 +120,11 @@ class Chain:
             batch = self.iqs[b0:b0 + self.qb]
             for j, iq in enumerate(batch):
                 self._timed("polarization", lambda: ctx.polarization(iq, G, self.P[j], self.prec))
-                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j], self.screen_prec)
+                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j], self.bose_prec)
             ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)],
                        self.screen_prec)
             for j, iq in enumerate(batch):
-                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt, self.screen_prec)
+                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt, self.bose_prec)
                 if self.Wkeep is not None:
                     self.Wkeep[b0 + j].copy_(self.Wt)
                 self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))

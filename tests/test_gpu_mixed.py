@@ -125,10 +125,12 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
     from paper_1602_02313_gb300.driver import Chain
     cr, gr = gi.make_config("nk64_nb64", nk=8)
     res = {}
-    for name, prec in [("fp64", gw.GW_FP64), ("fp16x2", gw.GW_FP16X2)]:
-        for cont in (gw.GW_PADE, gw.GW_CPE):
+    runs = [("fp64", gw.GW_FP64, None, (gw.GW_PADE, gw.GW_CPE)), ("fp16x2", gw.GW_FP16X2, None, (gw.GW_PADE, gw.GW_CPE)),
+            ("fp16x2_f32screen", gw.GW_FP16X2, gw.GW_F32, (gw.GW_CPE,))]
+    for name, prec, sprec, conts in runs:
+        for cont in conts:
             ctx = gw.GW(gr, cr, omega=gi.OMEGA_SI)
-            ch = Chain(ctx, dev(cr.eps), prec=prec, qb=4, cont_method=cont)
+            ch = Chain(ctx, dev(cr.eps), prec=prec, qb=4, cont_method=cont, screen_prec=sprec)
             ch.step()
             ch.check()
             res[(name, cont)] = {"eqp": host(ch.eqp).reshape(cr.nk, cr.nb), "sx": host(ch.Sx), "S": host(ch.S),
@@ -147,6 +149,13 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
         assert eS < 1e-3
     a, b = res[("fp64", gw.GW_CPE)], res[("fp16x2", gw.GW_CPE)]
     assert abs(gap(a["eqp"]) - gap(b["eqp"])) * ha2mev < 1.0  # the 1 meV target, CPE continuation
+    # the same with the dielectric solve in FP32 instead of float-float
+    c = res[("fp16x2_f32screen", gw.GW_CPE)]
+    dE, dgap = np.abs(a["eqp"] - c["eqp"]).max(), abs(gap(a["eqp"]) - gap(c["eqp"]))
+    print(f"chain nk=8 cpe, FP32 screening: Sigma^c rel err {rel(c['S'], a['S']):.3e}; max |dE_qp| "
+          f"{dE * ha2mev:.4f} meV; |dgap| {dgap * ha2mev:.4f} meV")
+    assert rel(c["S"], a["S"]) < 1e-3
+    assert dgap * ha2mev < 1.0
 
 
 def test_ni512_shapes_tc_vs_fp64(gw):
