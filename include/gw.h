@@ -183,7 +183,9 @@ gw_status gw_screen_static(int nq, int nnu, int ni, const double* sqrt_v, const 
  * Eq. (sigx) in the product basis with diagonal v:
  *             Sigx_n(k) += -1/(Omega N_k) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2.
  * G_tau [nk][nb][ntau]; occ [nk][nb]; Wt_tau cplx [ntau][ni][ni] (Hermitian);
- * Sigc_tau [nk][nb][ntau] (real: W~(tau) Hermitian); Sigx [nk][nb] (may be NULL). */
+ * Sigc_tau [nk][nb][ntau] (real: W~(tau) Hermitian); Sigx [nk][nb] (may be NULL).
+ * prec GW_FP64: both in FP64. GW_FP16X2 / GW_BF16X3: Sigc on the tensor cores, Sigx in
+ * float-float on the FP32 pipes (relative error ~1e-12). */
 gw_status gw_selfenergy(gw_ctx* ctx, int iq, const double* G_tau, const double* occ,
                         const double* Wt_tau, gw_prec prec, double* Sigc_tau, double* Sigx);
 

@@ -14,6 +14,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "cvt.cuh"
+
 namespace gwi {
 namespace arith {
 
@@ -55,7 +57,7 @@ struct F32 {
   static constexpr int kBlocksPerSm = 2;
   using S = float2;
   using Acc = float2;
-  __device__ static S from(double re, double im) { return make_float2(__double2float_rn(re), __double2float_rn(im)); }
+  __device__ static S from(double re, double im) { return make_float2(cvt::d2f(re), cvt::d2f(im)); }
   __device__ static double2 to(S v) { return make_double2((double)v.x, (double)v.y); }
   __device__ static S zero() { return make_float2(0.f, 0.f); }
   __device__ static Acc azero() { return make_float2(0.f, 0.f); }
@@ -78,9 +80,11 @@ struct Ff32 {
     float rh, rl, ih, il;
   };
   using Acc = S;
-  __device__ static S from(double re, double im) {
-    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
-    return {rh, __double2float_rn(re - (double)rh), ih, __double2float_rn(im - (double)ih)};
+  __device__ static S from(double re, double im) {  // hi = RN(x), lo = RN(x - hi), on the integer pipes
+    S v;
+    cvt::d2ff(re, v.rh, v.rl);
+    cvt::d2ff(im, v.ih, v.il);
+    return v;
   }
   __device__ static double2 to(S v) {
     return make_double2((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
@@ -139,8 +143,9 @@ struct Ff32 {
     float h, l;
   };
   __device__ static R rfrom(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
+    R r;
+    cvt::d2ff(x, r.h, r.l);
+    return r;
   }
   __device__ __forceinline__ static void ffadd(float ah, float al, float bh, float bl, float& h, float& l) {
     const float s = ah + bh;

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "arith.cuh"
+#include "cvt.cuh"
 #include "gw_internal.h"
 
 namespace gwi {
@@ -466,6 +467,66 @@ __global__ void k_vm(const double2* __restrict__ M, const double* __restrict__ v
   vm[(size_t)k * np + p] = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
 }
 
+// The same sum in float-float on the FP32 pipes (the mixed chain): M converted on the integer
+// pipes (cvt.cuh), |M|^2 = xh^2 + 2 xh xl + yh^2 + 2 yh yl with each product's rounding error
+// from an FMA (the xl^2, yl^2 terms lie below 2^-46 relative), times v_I in float-float, summed
+// by error-free two-sums into two alternating accumulators; ~1e-12 relative, against the
+// FP64 pipe's 3 operations per element, which bound k_vm on GB300.
+__device__ __forceinline__ void two_sum_ff(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+
+__device__ __forceinline__ void vm_term(double2 m, float vh, float vl, float& ah, float& al) {
+  float xh, xl, yh, yl;
+  cvt::d2ff(m.x, xh, xl);
+  cvt::d2ff(m.y, yh, yl);
+  const float p1 = __fmul_rn(xh, xh), p2 = __fmul_rn(yh, yh);  // never contracted into the sums below
+  float e1 = fmaf(xh, xh, -p1), e2 = fmaf(yh, yh, -p2);
+  e1 = fmaf(2.f * xh, xl, e1);
+  e2 = fmaf(2.f * yh, yl, e2);
+  float s, t;
+  two_sum_ff(p1, p2, s, t);
+  t += e1 + e2;
+  const float q = __fmul_rn(s, vh);
+  float eq = fmaf(s, vh, -q);
+  eq = fmaf(s, vl, eq);
+  eq = fmaf(t, vh, eq);
+  float c, ce;
+  two_sum_ff(ah, q, c, ce);
+  ah = c;
+  al += ce + eq;
+}
+
+__global__ void k_vm_ff(const double2* __restrict__ M, const double* __restrict__ v, int ni, int np,
+                        double* __restrict__ vm) {
+  extern __shared__ float2 svf[];  // v_I as (hi, lo)
+  for (int I = threadIdx.x; I < ni; I += blockDim.x) {
+    float h, l;
+    cvt::d2ff(v[I], h, l);
+    svf[I] = make_float2(h, l);
+  }
+  __syncthreads();
+  const int k = blockIdx.y;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const double2* Mk = M + (size_t)k * ni * np + p;
+  float ah[2] = {0.f, 0.f}, al[2] = {0.f, 0.f};
+  int I = 0;
+  for (; I + 8 <= ni; I += 8) {
+    double2 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Mk[(size_t)(I + u) * np];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) vm_term(m[u], svf[I + u].x, svf[I + u].y, ah[u & 1], al[u & 1]);
+  }
+  for (; I < ni; ++I) vm_term(Mk[(size_t)I * np], svf[I].x, svf[I].y, ah[0], al[0]);
+  float s, e;
+  two_sum_ff(ah[0], ah[1], s, e);
+  vm[(size_t)k * np + p] = (double)s + ((double)al[0] + (double)al[1] + (double)e);
+}
+
 __global__ void k_sigx_occ(const double* __restrict__ vm, const int* __restrict__ kmq, const double* __restrict__ occ,
                            int nk, int nb, double pref, double* __restrict__ Sx) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -478,7 +539,7 @@ __global__ void k_sigx_occ(const double* __restrict__ vm, const int* __restrict_
   Sx[e] += pref * s;
 }
 
-gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx) {
+gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx, bool ff) {
   const int np = c->nb * c->nb;
   const size_t need = (size_t)c->nk * np * sizeof(double);
   if (need > c->vm_bytes) {
@@ -493,7 +554,11 @@ gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx) {
   }
   const double2* M = (const double2*)m_block(c, iq);
   if (!M) return GW_ECUDA;
-  k_vm<<<dim3((np + 255) / 256, c->nk), 256, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->ni, np, c->d_vm);
+  if (ff)
+    k_vm_ff<<<dim3((np + 255) / 256, c->nk), 256, sizeof(float2) * c->ni, c->stream>>>(
+        M, c->d_v + (size_t)iq * c->ni, c->ni, np, c->d_vm);
+  else
+    k_vm<<<dim3((np + 255) / 256, c->nk), 256, 0, c->stream>>>(M, c->d_v + (size_t)iq * c->ni, c->ni, np, c->d_vm);
   gw_status s = check_launch(c, "sigx_vm");
   if (s != GW_OK) return s;
   const int n = c->nk * c->nb;
@@ -785,7 +850,7 @@ gw_status gw_selfenergy(gw_ctx* c, int iq, const double* G, const double* occ, c
   else
     return GW_EINVAL;
   if (st != GW_OK) return st;
-  if (Sx) return launch_sigx(c, iq, occ, Sx);
+  if (Sx) return launch_sigx(c, iq, occ, Sx, prec != GW_FP64);  // float-float on the mixed chain
   return GW_OK;
 }
 

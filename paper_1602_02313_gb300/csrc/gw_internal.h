@@ -143,7 +143,7 @@ gw_status launch_screen(gw_ctx* c, int iq0, int nqb, int prec, const double* P, 
                         double* aug);
 gw_status launch_sigma_fp64(gw_ctx* c, int iq, const double* G, const double* W, double* S);
 gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W, int prec, double* S);
-gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx);
+gw_status launch_sigx(gw_ctx* c, int iq, const double* occ, double* Sx, bool ff);
 gw_status launch_continue(gw_ctx* c, int method, int64_t nprob, const double* sig_iw, const double* eps,
                           const double* sigx, const double* vxc, int nreal, const double* omega_real,
                           double* sig_real, double* e_qp, int* info);

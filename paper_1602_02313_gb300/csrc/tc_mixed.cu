@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "cvt.cuh"
 #include "gw_internal.h"
 #include "tc_common.cuh"
 
@@ -121,8 +122,8 @@ __global__ void k_split_y(const double2* __restrict__ Mq, int nk, int ni, int np
   for (int q = 0; q < 8; ++q) {
     double2 v = make_double2(0.0, 0.0);
     if (pb + q < np) v = Mq[((size_t)k * ni + I) * np + pb + q];
-    split2((float)v.x * kScaleA, rh.v[q], rl.v[q]);
-    split2((float)v.y * kScaleA, ih.v[q], il.v[q]);
+    split2(cvt::d2f(v.x) * kScaleA, rh.v[q], rl.v[q]);
+    split2(cvt::d2f(v.y) * kScaleA, ih.v[q], il.v[q]);
   }
   const int iblk = I >> 7, r = I & 127;
   __half* hi = YS + ys_tile(k, c, iblk, 0, cpk, nib);
@@ -404,9 +405,8 @@ __global__ void __launch_bounds__(256) k_split_x(const double2* __restrict__ Mq,
 #pragma unroll
   for (int j = 0; j < SX_I / 8; ++j) {
     const int r = ty + 8 * j, I = I0 + r;
-    // scaled after the conversion (a power of two: the same value, one FP64-pipe operation
-    // fewer per component)
-    const float2 f = make_float2(__double2float_rn(v[j].x) * kScaleA, __double2float_rn(v[j].y) * kScaleA);
+    // converted on the integer pipes, then scaled (a power of two: the same value)
+    const float2 f = make_float2(cvt::d2f(v[j].x) * kScaleA, cvt::d2f(v[j].y) * kScaleA);
     tileF[r][tx ^ (2 * ((r >> 4) & 3))] = f;
     if (I < ni) XE[(((size_t)k * npb + (p >> 7)) * ni + I) * 128 + (p & 127)] = f;
   }

@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 TOL_P = 2e-5
 TOL_S = 2e-5
+TOL_SX_FF = 1e-11  # float-float exchange sum: ~2^-44 per term, 256-term positive sums
 
 
 @pytest.fixture(scope="module")
@@ -77,17 +78,22 @@ def test_selfenergy_tc(gw, name, case):
     G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
     rng = np.random.default_rng(11)
     S = zeros((cr.nk, cr.nb, gr.ntau))
+    Sx = zeros((cr.nk, cr.nb))
     Sref = np.zeros((cr.nk, cr.nb, gr.ntau))
+    Sxref = np.zeros((cr.nk, cr.nb))
     for iq in range(cr.nq):
         X = rng.standard_normal((gr.ntau, cr.ni, cr.ni)) + 1j * rng.standard_normal((gr.ntau, cr.ni, cr.ni))
         W = -30.0 * (X @ np.conj(np.swapaxes(X, 1, 2))) / cr.ni
-        ctx.selfenergy(iq, dev(G), dev(occ), dev(W), S, None, gw.GW_FP16X2)
-        sc, _, _ = orc.selfenergy(gi.m_for_q(cr, iq), G, W, cr.v[iq], cr.kmq[iq], occ)
+        ctx.selfenergy(iq, dev(G), dev(occ), dev(W), S, Sx, gw.GW_FP16X2)
+        sc, sx, _ = orc.selfenergy(gi.m_for_q(cr, iq), G, W, cr.v[iq], cr.kmq[iq], occ)
         Sref += sc
+        Sxref += sx
     ctx.sync()
     e = rel(host(S), Sref)
-    print(f"{name}: Sigma tensor-core rel err {e:.3e}")
+    ex = rel(host(Sx), Sxref)
+    print(f"{name}: Sigma tensor-core rel err {e:.3e}; Sigma^x float-float rel err {ex:.3e}")
     assert e < TOL_S
+    assert ex < TOL_SX_FF
 
 
 def test_c2_full_size_tc_vs_fp64(gw):
@@ -110,12 +116,16 @@ def test_c2_full_size_tc_vs_fp64(gw):
     W = dev(-(X @ np.conj(np.swapaxes(X, 1, 2))) * 5.0)
     S64 = zeros((cr.nk, cr.nb, gr.ntau))
     S16 = zeros((cr.nk, cr.nb, gr.ntau))
-    ctx.selfenergy(0, Gd, dev(occ), W, S64, None, gw.GW_FP64)
-    ctx.selfenergy(0, Gd, dev(occ), W, S16, None, gw.GW_FP16X2)
+    Sx64 = zeros((cr.nk, cr.nb))
+    Sx16 = zeros((cr.nk, cr.nb))
+    ctx.selfenergy(0, Gd, dev(occ), W, S64, Sx64, gw.GW_FP64)
+    ctx.selfenergy(0, Gd, dev(occ), W, S16, Sx16, gw.GW_FP16X2)
     ctx.sync()
     e = rel(host(S16), host(S64))
-    print(f"Nk=64: Sigma tensor-core vs FP64 rel err {e:.3e}")
+    ex = rel(host(Sx16), host(Sx64))
+    print(f"Nk=64: Sigma tensor-core vs FP64 rel err {e:.3e}; Sigma^x float-float vs FP64 {ex:.3e}")
     assert e < TOL_S
+    assert ex < TOL_SX_FF
 
 
 def test_chain_qp_gap_mixed_vs_fp64(gw):
@@ -125,8 +135,9 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
     from paper_1602_02313_gb300.driver import Chain
     cr, gr = gi.make_config("nk64_nb64", nk=8)
     res = {}
+    # the mixed chain as the bench runs it (FP32 dielectric solve), and with the float-float solve
     runs = [("fp64", gw.GW_FP64, None, (gw.GW_PADE, gw.GW_CPE)), ("fp16x2", gw.GW_FP16X2, None, (gw.GW_PADE, gw.GW_CPE)),
-            ("fp16x2_f32screen", gw.GW_FP16X2, gw.GW_F32, (gw.GW_CPE,))]
+            ("fp16x2_ffscreen", gw.GW_FP16X2, gw.GW_F32X2, (gw.GW_CPE,))]
     for name, prec, sprec, conts in runs:
         for cont in conts:
             ctx = gw.GW(gr, cr, omega=gi.OMEGA_SI)
@@ -149,10 +160,10 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
         assert eS < 1e-3
     a, b = res[("fp64", gw.GW_CPE)], res[("fp16x2", gw.GW_CPE)]
     assert abs(gap(a["eqp"]) - gap(b["eqp"])) * ha2mev < 1.0  # the 1 meV target, CPE continuation
-    # the same with the dielectric solve in FP32 instead of float-float
-    c = res[("fp16x2_f32screen", gw.GW_CPE)]
+    # the same with the dielectric solve in float-float instead of FP32
+    c = res[("fp16x2_ffscreen", gw.GW_CPE)]
     dE, dgap = np.abs(a["eqp"] - c["eqp"]).max(), abs(gap(a["eqp"]) - gap(c["eqp"]))
-    print(f"chain nk=8 cpe, FP32 screening: Sigma^c rel err {rel(c['S'], a['S']):.3e}; max |dE_qp| "
+    print(f"chain nk=8 cpe, float-float screening: Sigma^c rel err {rel(c['S'], a['S']):.3e}; max |dE_qp| "
           f"{dE * ha2mev:.4f} meV; |dgap| {dgap * ha2mev:.4f} meV")
     assert rel(c["S"], a["S"]) < 1e-3
     assert dgap * ha2mev < 1.0
