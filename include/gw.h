@@ -143,6 +143,15 @@ gw_status gw_polarization(gw_ctx* ctx, int iq, const double* G_tau, gw_prec prec
 gw_status gw_tau_to_freq(gw_ctx* ctx, gw_stat stat, gw_dir dir, int64_t batch, const double* in,
                          gw_prec prec, double* out);
 
+/* count independent transforms of gw_tau_to_freq in one call, their inputs and outputs stored
+ * one after another (in [count][...in of one transform], out [count][...out of one]); the
+ * bosonic directions run them in one grid (q points of a block of the chain), the fermionic
+ * ones as one batch of count * batch rows. Results are those of count separate calls.
+ * 1 <= count <= 65535, else GW_EINVAL. Float-float inputs are converted through a context
+ * workspace in chunks of at most 2 GiB. */
+gw_status gw_tau_to_freq_many(gw_ctx* ctx, gw_stat stat, gw_dir dir, int count, int64_t batch, const double* in,
+                              gw_prec prec, double* out);
+
 /* Screened interaction minus bare Coulomb, W~ = W - v (Sec. III.B.3), at the bosonic
  * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2, X = (1 - Pi)^-1 Pi,
  * W~ = v^1/2 X v^1/2, for the nqb q points iq0 .. iq0 + nqb - 1 at once. With ni a

@@ -262,10 +262,13 @@ static gw_status grow_ws(gw_ctx* c, size_t need) {
 template <int JB, class AR>
 __global__ void k_bose_fwd(const double2* __restrict__ T, const typename AR::S* __restrict__ in,
                            double2* __restrict__ out, int64_t batch, int ntau, int nf) {
-  // block (x, y): 128 batch elements x frequencies j0 .. j0 + JB - 1 (grid.y = ceil(nf / JB))
+  // block (x, y, z): 128 batch elements x frequencies j0 .. j0 + JB - 1 (grid.y = ceil(nf / JB))
+  // of transform z
   using S = typename AR::S;
   extern __shared__ __align__(16) unsigned char bfsm[];
   S* sT = reinterpret_cast<S*>(bfsm);
+  in += (size_t)blockIdx.z * ntau * batch;  // grid.z: consecutive transforms of one call
+  out += (size_t)blockIdx.z * nf * batch;
   const int j0 = blockIdx.y * JB, nj = min(JB, nf - j0);
   for (int i = threadIdx.x; i < nj * ntau; i += blockDim.x) {
     const double2 t = T[(size_t)j0 * ntau + i];
@@ -296,11 +299,22 @@ template <int IB, class AR, bool PRE>
 __global__ void k_bose_bwd(const double* __restrict__ Tb, const double2* __restrict__ W,
                            const typename AR::S* __restrict__ Gh, const typename AR::S* __restrict__ Hh,
                            double2* __restrict__ out, int m, int ntau, int nf) {
-  // block (x, y): 128 matrix elements x tau points i0 .. i0 + IB - 1 (grid.y = ceil(ntau / IB))
+  // block (x, y, z): 128 matrix elements x tau points i0 .. i0 + IB - 1 (grid.y = ceil(ntau / IB))
+  // of transform z
   using S = typename AR::S;
   using R = typename AR::R;
   extern __shared__ __align__(16) unsigned char bbsm[];
   R* sTb = reinterpret_cast<R*>(bbsm);
+  {
+    const size_t zq = (size_t)blockIdx.z * m * m;
+    if (PRE) {
+      Gh += zq * nf;
+      Hh += zq * nf;
+    } else {
+      W += zq * nf;
+    }
+    out += zq * ntau;
+  }
   const int i0 = blockIdx.y * IB, ni = min(IB, ntau - i0);
   for (int i = threadIdx.x; i < ni * 2 * nf; i += blockDim.x) sTb[i] = AR::rfrom(Tb[(size_t)i0 * 2 * nf + i]);
   __syncthreads();
@@ -368,29 +382,39 @@ __global__ void k_fermi_bwd(const double* __restrict__ Tb, const double2* __rest
   out[e] = s;
 }
 
-gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch, const double* in, double* out) {
+// Float-float conversions of a multi-transform call go through the workspace in chunks of
+// transforms of at most this many bytes.
+constexpr size_t kFfWsCap = 2ull << 30;
+
+gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int count, int64_t batch, const double* in,
+                           double* out) {
   const int nt = c->ntau;
   if (stat == GW_BOSE && dir == GW_TAU_TO_IW) {
     const int64_t blocks = (batch + 127) / 128;
     if (prec == GW_F32X2) {
       using S = arith::Ff32::S;
-      const int64_t n = (int64_t)nt * batch;
+      const int64_t per = (int64_t)nt * batch;  // inputs of one transform
+      const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(count, kFfWsCap / (sizeof(S) * per)));
       gw_status st;
-      if ((st = grow_ws(c, sizeof(S) * n)) != GW_OK) return st;
-      k_to_ff<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, (S*)c->ff_ws, n);
-      if ((st = check_launch(c, "to_ff")) != GW_OK) return st;
+      if ((st = grow_ws(c, sizeof(S) * per * chunk)) != GW_OK) return st;
       const size_t sm = sizeof(S) * 16 * nt;
       if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<16, arith::Ff32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_fwd<16, arith::Ff32><<<dim3((unsigned)blocks, (c->nnu + 15) / 16), 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
-                                                                             (const S*)c->ff_ws, (double2*)out, batch,
-                                                                             nt, c->nnu);
-    } else {
-      const size_t sm = sizeof(double2) * 8 * nt;
-      if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_fwd<8, arith::Fp64><<<dim3((unsigned)blocks, (c->nnu + 7) / 8), 128, sm, c->stream>>>((const double2*)c->d_Bfwd,
-                                                                            (const double2*)in, (double2*)out, batch,
-                                                                            nt, c->nnu);
+      for (int z0 = 0; z0 < count; z0 += chunk) {
+        const int nz = std::min(chunk, count - z0);
+        const int64_t n = per * nz;
+        k_to_ff<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in + per * z0, (S*)c->ff_ws, n);
+        if ((st = check_launch(c, "to_ff")) != GW_OK) return st;
+        k_bose_fwd<16, arith::Ff32><<<dim3((unsigned)blocks, (c->nnu + 15) / 16, nz), 128, sm, c->stream>>>(
+            (const double2*)c->d_Bfwd, (const S*)c->ff_ws, (double2*)out + (int64_t)c->nnu * batch * z0, batch, nt,
+            c->nnu);
+        if ((st = check_launch(c, "bose_fwd")) != GW_OK) return st;
+      }
+      return GW_OK;
     }
+    const size_t sm = sizeof(double2) * 8 * nt;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_bose_fwd<8, arith::Fp64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bose_fwd<8, arith::Fp64><<<dim3((unsigned)blocks, (c->nnu + 7) / 8, count), 128, sm, c->stream>>>(
+        (const double2*)c->d_Bfwd, (const double2*)in, (double2*)out, batch, nt, c->nnu);
     return check_launch(c, "bose_fwd");
   }
   if (stat == GW_BOSE && dir == GW_IW_TO_TAU) {
@@ -399,27 +423,37 @@ gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int64_t batch
     const unsigned blocks = (unsigned)((mm + 127) / 128);
     if (prec == GW_F32X2) {
       using S = arith::Ff32::S;
-      const int64_t n = (int64_t)c->nnu * mm;
+      const int64_t per = (int64_t)c->nnu * mm;  // inputs of one transform
+      const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(count, kFfWsCap / (2 * sizeof(S) * per)));
       gw_status st;
-      if ((st = grow_ws(c, 2 * sizeof(S) * n)) != GW_OK) return st;
-      S* Gh = (S*)c->ff_ws;
-      S* Hh = Gh + n;
-      k_to_ff_sym<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in, m, c->nnu, Gh, Hh);
-      if ((st = check_launch(c, "to_ff_sym")) != GW_OK) return st;
+      if ((st = grow_ws(c, 2 * sizeof(S) * per * chunk)) != GW_OK) return st;
       const size_t sm = sizeof(arith::Ff32::R) * 16 * 2 * c->nnu;
       if (sm > 48 * 1024)
         cudaFuncSetAttribute(k_bose_bwd<16, arith::Ff32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<16, arith::Ff32, true><<<dim3(blocks, (nt + 15) / 16), 128, sm, c->stream>>>(c->d_Bbwd, nullptr, Gh, Hh, (double2*)out, m,
-                                                                         nt, c->nnu);
-    } else {
-      const size_t sm = sizeof(double) * 8 * 2 * c->nnu;
-      if (sm > 48 * 1024)
-        cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      k_bose_bwd<8, arith::Fp64, false><<<dim3(blocks, (nt + 7) / 8), 128, sm, c->stream>>>(c->d_Bbwd, (const double2*)in, nullptr,
-                                                                         nullptr, (double2*)out, m, nt, c->nnu);
+      for (int z0 = 0; z0 < count; z0 += chunk) {
+        const int nz = std::min(chunk, count - z0);
+        const int64_t n = per * nz;
+        S* Gh = (S*)c->ff_ws;
+        S* Hh = Gh + n;
+        // nz consecutive transforms are one [nz nnu][m][m] stack for the symmetrisation
+        k_to_ff_sym<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>((const double2*)in + per * z0, m,
+                                                                         (int64_t)c->nnu * nz, Gh, Hh);
+        if ((st = check_launch(c, "to_ff_sym")) != GW_OK) return st;
+        k_bose_bwd<16, arith::Ff32, true><<<dim3(blocks, (nt + 15) / 16, nz), 128, sm, c->stream>>>(
+            c->d_Bbwd, nullptr, Gh, Hh, (double2*)out + (int64_t)nt * mm * z0, m, nt, c->nnu);
+        if ((st = check_launch(c, "bose_bwd")) != GW_OK) return st;
+      }
+      return GW_OK;
     }
+    const size_t sm = sizeof(double) * 8 * 2 * c->nnu;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(k_bose_bwd<8, arith::Fp64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_bose_bwd<8, arith::Fp64, false><<<dim3(blocks, (nt + 7) / 8, count), 128, sm, c->stream>>>(
+        c->d_Bbwd, (const double2*)in, nullptr, nullptr, (double2*)out, m, nt, c->nnu);
     return check_launch(c, "bose_bwd");
   }
+  // FERMI: count consecutive [batch][...] blocks are one batch of count * batch rows
+  batch *= count;
   if (stat == GW_FERMI && (dir == GW_TAU_TO_IW || dir == GW_TAU_TO_IW_CONT)) {
     const int nf = dir == GW_TAU_TO_IW ? c->nw : c->ncont;
     const double* T = dir == GW_TAU_TO_IW ? c->d_Ffwd : c->d_Fcont;
@@ -814,13 +848,18 @@ gw_status gw_polarization(gw_ctx* c, int iq, const double* G, gw_prec prec, doub
   return GW_EINVAL;
 }
 
-gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, const double* in, gw_prec prec,
-                         double* out) {
-  if (!c || !in || !out || batch <= 0) return GW_EINVAL;
+gw_status gw_tau_to_freq_many(gw_ctx* c, gw_stat stat, gw_dir dir, int count, int64_t batch, const double* in,
+                              gw_prec prec, double* out) {
+  if (!c || !in || !out || batch <= 0 || count <= 0 || count > 65535) return GW_EINVAL;
   if (stat == GW_BOSE && dir == GW_TAU_TO_IW_CONT) return GW_EINVAL;
   if (prec != GW_FP64 && !(prec == GW_F32X2 && stat == GW_BOSE))
     return set_err(c, GW_EUNSUPPORTED, "gw_tau_to_freq: GW_FP64, or GW_F32X2 for the bosonic transforms");
-  return launch_transform(c, (int)stat, (int)dir, (int)prec, batch, in, out);
+  return launch_transform(c, (int)stat, (int)dir, (int)prec, count, batch, in, out);
+}
+
+gw_status gw_tau_to_freq(gw_ctx* c, gw_stat stat, gw_dir dir, int64_t batch, const double* in, gw_prec prec,
+                         double* out) {
+  return gw_tau_to_freq_many(c, stat, dir, 1, batch, in, prec, out);
 }
 
 gw_status gw_screen(gw_ctx* c, int iq0, int nqb, const double* P, gw_prec prec, double* W, int* info) {

@@ -66,7 +66,7 @@ class Chain:
         self.P = torch.zeros(self.qb, nt, ni, ni, dtype=c16, **d)
         self.Piv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
         self.Wiv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
-        self.Wt = torch.zeros(nt, ni, ni, dtype=c16, **d)
+        self.Wt = torch.zeros(self.qb, nt, ni, ni, dtype=c16, **d)
         self.info = torch.zeros(self.qb, self.nnu, dtype=torch.int32, **d)
         self.Siw = torch.zeros(nk, nb, self.nw, dtype=c16, **d)
         self.Siwc = torch.zeros(nk, nb, self.ncont, dtype=c16, **d)
@@ -118,16 +118,17 @@ class Chain:
         ni = self.ni
         for b0 in range(0, len(self.iqs), self.qb):
             batch = self.iqs[b0:b0 + self.qb]
+            nb_ = len(batch)
             for j, iq in enumerate(batch):
                 self._timed("polarization", lambda: ctx.polarization(iq, G, self.P[j], self.prec))
-                ctx.tau_to_freq(GW_BOSE, GW_TAU_TO_IW, ni * ni, self.P[j], self.Piv[j], self.bose_prec)
-            ctx.screen(batch[0], len(batch), self.Piv[:len(batch)], self.Wiv[:len(batch)], self.info[:len(batch)],
-                       self.screen_prec)
+            # the block's q points in one grid per direction
+            ctx.tau_to_freq_many(GW_BOSE, GW_TAU_TO_IW, nb_, ni * ni, self.P, self.Piv, self.bose_prec)
+            ctx.screen(batch[0], nb_, self.Piv[:nb_], self.Wiv[:nb_], self.info[:nb_], self.screen_prec)
+            ctx.tau_to_freq_many(GW_BOSE, GW_IW_TO_TAU, nb_, ni, self.Wiv, self.Wt, self.bose_prec)
             for j, iq in enumerate(batch):
-                ctx.tau_to_freq(GW_BOSE, GW_IW_TO_TAU, ni, self.Wiv[j], self.Wt, self.bose_prec)
                 if self.Wkeep is not None:
-                    self.Wkeep[b0 + j].copy_(self.Wt)
-                self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt, self.S, self.Sx, self.prec))
+                    self.Wkeep[b0 + j].copy_(self.Wt[j])
+                self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt[j], self.S, self.Sx, self.prec))
 
     def sigma_fixed_w(self, G, occ):
         """Sigma^c(tau), Sigma^x from G with the W~(tau) kept by the first pass (GW0)."""

@@ -77,3 +77,4 @@ def test_invalid_arguments_rejected_on_host(gw):
     assert lib.gw_set_tuning(None, gw.GW_TUNE_POL_SEG_CHUNKS, 16) == gw.GW_EINVAL
     assert lib.gw_kernel_timing(None, 1) == gw.GW_EINVAL
     assert lib.gw_measure_alu(0, None, None) == gw.GW_EINVAL
+    assert lib.gw_tau_to_freq_many(None, gw.GW_BOSE, gw.GW_TAU_TO_IW, 1, 1, None, gw.GW_FP64, None) == gw.GW_EINVAL

@@ -131,6 +131,20 @@ def test_transforms(gw, case):
     e_bwd = rel(host(Wt), orc.transforms.apply_bwd_hermitian(T["B_bwd_re"], T["B_bwd_im"], W))
     print(f"bosonic transforms in float-float: fwd {e_fwd:.1e}, bwd {e_bwd:.1e}")
     assert e_fwd < TOL_F32X2_T and e_bwd < TOL_F32X2_T
+    # three transforms in one call (grid.z): the results of three separate calls, bit for bit
+    for prec in (gw.GW_FP64, gw.GW_F32X2):
+        x3 = rng.standard_normal((3, gr.ntau, m, m)) + 1j * rng.standard_normal((3, gr.ntau, m, m))
+        W3 = rng.standard_normal((3, gr.nnu, m, m)) + 1j * rng.standard_normal((3, gr.nnu, m, m))
+        y3, Wt3 = zeros((3, gr.nnu, m, m), "c16"), zeros((3, gr.ntau, m, m), "c16")
+        ctx.tau_to_freq_many(gw.GW_BOSE, gw.GW_TAU_TO_IW, 3, m * m, dev(x3), y3, prec)
+        ctx.tau_to_freq_many(gw.GW_BOSE, gw.GW_IW_TO_TAU, 3, m, dev(W3), Wt3, prec)
+        for z in range(3):
+            y1, Wt1 = zeros((gr.nnu, m, m), "c16"), zeros((gr.ntau, m, m), "c16")
+            ctx.tau_to_freq(gw.GW_BOSE, gw.GW_TAU_TO_IW, m * m, dev(x3[z]), y1, prec)
+            ctx.tau_to_freq(gw.GW_BOSE, gw.GW_IW_TO_TAU, m, dev(W3[z]), Wt1, prec)
+            ctx.sync()
+            assert np.array_equal(host(y3)[z], host(y1))
+            assert np.array_equal(host(Wt3)[z], host(Wt1))
     s = rng.standard_normal((29, gr.ntau))
     for d, key, nf in [(gw.GW_TAU_TO_IW, "F_fwd", gr.nw), (gw.GW_TAU_TO_IW_CONT, "F_cont", gr.ncont)]:
         o = zeros((29, nf), "c16")
