@@ -322,6 +322,37 @@ def make_grid(beta, ntau, nnu, nw, ncont=128, tau_min=1e-3, lam=None, tol=1e-10)
                 w_idx=w_idx, ncont=int(ncont))
 
 
+# ---------------------------------------------------------------------------
+# Uniform power mesh (tau-domain screening, Sec. III.A / III.B.3)
+# ---------------------------------------------------------------------------
+def upm_grid(beta, p, m):
+    """Uniform power mesh UPM(p, m) on [0, beta] (Sec. III.A, after Ku-Eguiluz and Stan et al.),
+    2 p m + 1 points including 0 and beta. Reading of the paper's description: on [0, beta/2]
+    the sub-interval ends are 0 and (beta/2) 2^(k - p), k = 1..p (widths beta 2^-p, beta 2^-p,
+    beta 2^(1-p), ..., beta/4), each divided into m equal steps; the mesh is mirrored by
+    tau -> beta - tau, so it is densest at both ends."""
+    ends = [0.0] + [0.5 * beta * 2.0 ** (k - p) for k in range(1, p + 1)]
+    half = []
+    for a, b in zip(ends[:-1], ends[1:]):
+        half.extend(a + (b - a) * np.arange(m) / m)
+    half = np.array(half + [0.5 * beta])
+    return np.concatenate([half, beta - half[-2::-1]])
+
+
+def tau_pairs(tau, beta, rtol=1e-11):
+    """The distinct differences d = (tau_p - tau_r) mod beta in [0, beta) of a mesh and, for every
+    pair, the index of its difference: returns (d [ndiff], idx int [npts][npts]). Differences of
+    0 and +-beta are all d = 0 (bosonic periodicity). Values equal up to rounding share one index."""
+    tau = np.asarray(tau, float)
+    d = tau[:, None] - tau[None, :]
+    d = np.where(d < 0.0, d + beta, d)
+    d = np.where(d >= beta * (1.0 - rtol), d - beta, d)
+    d = np.where(np.abs(d) < beta * rtol, 0.0, d)
+    key = np.round(d / (beta * rtol)).astype(np.int64)
+    _, first, inv = np.unique(key.ravel(), return_index=True, return_inverse=True)
+    return d.ravel()[first], inv.reshape(d.shape).astype(np.int32)
+
+
 # Unit-cell volume Omega of 1/(Omega N_k) (Eqs. irpol, sigc): the paper's silicon cell,
 # a = 5.43 Angstrom (Sec. IV), primitive fcc volume a^3 / 4 in bohr^3.
 OMEGA_SI = (5.43 / 0.529177210903) ** 3 / 4.0

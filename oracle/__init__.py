@@ -27,9 +27,13 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
 * pade / cpe / qp   -- analytic continuation (Sec. III.B.6); pinned by exact
                        recovery of few-pole models and causality.
 * mlp               -- not in the paper; pinned by central finite differences.
+* screen_tau        -- the paper's tau-domain form of Eq. (tildeW) on the uniform power
+                       mesh (Sec. III.B.3); pinned by closed forms of one-mode and
+                       exponential polarizations (second and first order in the step).
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401
 from . import mlp  # noqa: F401
+from . import screen_tau  # noqa: F401
 from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
                            cpe_eval, qp_solve, band_gap, pade_resig, cpe_resig, ETA)

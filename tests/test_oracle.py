@@ -396,3 +396,77 @@ def test_mlp_gradient_finite_differences():
     z = np.linspace(-30, 30, 13)
     assert np.all(mlp.softplus(z) >= 0)
     assert np.allclose((mlp.softplus(z + 1e-6) - mlp.softplus(z - 1e-6)) / 2e-6, mlp.sigmoid(z), atol=1e-8)
+
+
+# ------------------------------------------------------------------ tau-domain screening (Eq. tildeW, Sec. III.B.3)
+def test_upm_grid_and_increments():
+    beta = 50.0
+    for p, m in [(3, 2), (5, 4), (8, 3)]:
+        t = gi.upm_grid(beta, p, m)
+        assert len(t) == 2 * p * m + 1
+        assert t[0] == 0.0 and t[-1] == beta and np.all(np.diff(t) > 0)
+        assert np.allclose(t + t[::-1], beta, rtol=0, atol=1e-12 * beta)
+        assert np.isclose(np.diff(t).min(), beta / 2 ** p / m)      # densest at the ends
+        dt = orc.screen_tau.trapezoid_weights(t)
+        # the increments of the paper are the trapezoid rule: exact on linear functions
+        assert np.isclose(dt.sum(), beta, rtol=1e-14)
+        assert np.isclose(dt @ (3.0 * t - 1.0), 1.5 * beta ** 2 - beta, rtol=1e-13)
+        d, idx = gi.tau_pairs(t, beta)
+        assert np.allclose(d[idx], np.mod(t[:, None] - t[None, :], beta) % beta, atol=1e-9)
+        assert idx[0, 0] == idx[-1, 0] == idx[0, -1] and d[idx[0, 0]] == 0.0   # 0 and +-beta are P(0)
+
+
+def _scalar_case(model, p, m, beta=20.0, a=0.3, E=0.8, v=2.0):
+    st = orc.screen_tau
+    t = gi.upm_grid(beta, p, m)
+    d, idx = gi.tau_pairs(t, beta)
+    if model == "pole":
+        Pd, ex = st.single_pole_P(d, a, E, beta), st.single_pole_Wt(t, a, E, v, beta)
+    else:  # exponential: not symmetric under tau -> beta - tau, so the pair order matters
+        Pd = -a * np.exp(-E * d) / (1.0 - np.exp(-beta * E))
+        Ep = E + a * v
+        ex = -a * v * v * np.exp(-Ep * t) / (1.0 - np.exp(-beta * Ep))
+    W = st.screen_tau(Pd[idx][:, :, None, None], np.array([v]), t)[:, 0, 0]
+    # the exponential model jumps at tau = 0 mod beta; W~(beta) is W~(0^-), compare below it
+    sl = slice(None) if model == "pole" else slice(0, -1)
+    return np.abs(W[sl] - ex[sl]).max() / np.abs(ex).max()
+
+
+def test_screen_tau_single_pole_closed_form():
+    """One bosonic mode P(i nu) = -2 a E / (nu^2 + E^2): W~(tau) = -a v^2 E cosh(Om (tau - beta/2)) /
+    (Om sinh(Om beta/2)), Om^2 = E^2 + 2 a v E. The trapezoid solve converges at second order."""
+    e = [_scalar_case("pole", 3, m) for m in (4, 8, 16, 32)]
+    assert all(e[i] / e[i + 1] > 3.5 for i in range(3)), e
+    assert e[-1] < 1e-3
+
+
+def test_screen_tau_exponential_closed_form():
+    """P(tau) = -a e^{-E tau} / (1 - e^{-beta E}) (P(i nu) = -a / (E - i nu)): W~(tau) = -a v^2 e^{-E' tau} /
+    (1 - e^{-beta E'}), E' = E + a v. P jumps at tau = 0 mod beta, so first order; the wrong pair order
+    (P(tau_r - tau_p)) converges to W~(beta - tau) instead."""
+    e = [_scalar_case("exp", 3, m) for m in (8, 16, 32)]
+    assert all(e[i] / e[i + 1] > 1.7 for i in range(2)), e
+    assert e[-1] < 0.06
+
+
+def test_screen_tau_matrix_in_common_eigenbasis():
+    """NI = 3, uniform v and P(tau) = U diag(p_s(tau)) U^dagger with one mode per direction: W~(tau) =
+    U diag(W_s(tau)) U^dagger from the scalar closed forms; also Hermitian at every tau."""
+    st = orc.screen_tau
+    rng = np.random.default_rng(17)
+    beta, v, ni = 20.0, 1.5, 3
+    a = np.array([0.2, 0.5, 0.9])
+    E = np.array([0.4, 1.1, 2.0])
+    U, _ = np.linalg.qr(rng.standard_normal((ni, ni)) + 1j * rng.standard_normal((ni, ni)))
+    errs = []
+    for m in (16, 32):
+        t = gi.upm_grid(beta, 3, m)
+        d, idx = gi.tau_pairs(t, beta)
+        Pd = np.einsum("is,ns,js->nij", U, np.stack([st.single_pole_P(d, a[s], E[s], beta) for s in range(ni)], 1),
+                       U.conj())
+        W = st.screen_tau(Pd[idx], np.full(ni, v), t)
+        Wex = np.einsum("is,ns,js->nij", U,
+                        np.stack([st.single_pole_Wt(t, a[s], E[s], v, beta) for s in range(ni)], 1), U.conj())
+        errs.append(np.abs(W - Wex).max() / np.abs(Wex).max())
+        assert np.abs(W - np.conj(np.swapaxes(W, 1, 2))).max() < 1e-12 * np.abs(W).max()
+    assert errs[0] / errs[1] > 3.5 and errs[1] < 5e-3, errs
