@@ -212,6 +212,80 @@ def run_batch(args, prec):
     torch.cuda.synchronize()
 
 
+def run_tau_screen(args):
+    """The paper's tau-domain form of Eq. (tildeW) (gw_screen_tau) on the Nk=8 crystal's basis
+    (NI = 64, beta = 100) and the uniform power mesh UPM(4, 2) (17 points): one dense solve of
+    1088 unknowns with 64 right-hand sides. A cross-check of the i nu route, not a step of the
+    benchmarked iteration; timed alone, one GPU."""
+    import torch
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    b.build()
+    cr, gr = gi.make_config("nk8_nb16")
+    p_, m_ = 4, 2
+    tau = gi.upm_grid(gr.beta, p_, m_)
+    npts, ni = len(tau), cr.ni
+    # synthetic polarization at every mesh difference: four bosonic modes with random Hermitian
+    # negative semidefinite weights (P(i nu) = -sum_s B_s B_s^+ 2 E_s / (nu^2 + E_s^2))
+    d, idx = gi.tau_pairs(tau, gr.beta)
+    rng = np.random.default_rng(20260)
+    P = np.zeros((len(d), ni, ni), complex)
+    for E in (0.3, 0.7, 1.2, 2.0):
+        B = (rng.standard_normal((ni, 8)) + 1j * rng.standard_normal((ni, 8))) * (0.02 / np.sqrt(ni))
+        shape = np.cosh(E * (d - 0.5 * gr.beta)) / np.sinh(0.5 * E * gr.beta)
+        P -= shape[:, None, None] * (B @ B.conj().T)[None]
+    Pp = np.ascontiguousarray(P[idx])
+    ctx = gw.GW(gr, cr, omega=args.omega)
+    Pd = torch.from_numpy(Pp).cuda()
+    W = torch.zeros((npts, ni, ni), dtype=torch.complex128, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    ctx.set_stream(s)
+    for _ in range(args.warmup):
+        ctx.screen_tau(0, tau, Pd, W, info)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed solves only
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        ctx.screen_tau(0, tau, Pd, W, info)
+    e1.record(s)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.launch_count() - launches0
+    assert int(info.item()) == 0
+    N, L = npts * ni, npts * ni + ni
+    macs = float(sum(N * (L - k) for k in range(N)))  # complex multiply-adds of the elimination
+    fp64_tf, _ = gw.measure_alu(0)
+    ach = 8.0 * macs / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_tsys_step (all N pivot steps of one solve, CUDA events around the call)",
+            "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s FP64", "frac": ach / fp64_tf,
+            "peak_source": "measured FP64 FMA rate of this GPU (gw_measure_alu, this run)",
+            "flops_per_solve": 8.0 * macs}
+    cpu = None
+    if not args.no_cpu:
+        import oracle as orc
+        t0 = time.perf_counter()
+        ref = orc.screen_tau.screen_tau(Pp, cr.v[0], tau)
+        tc = time.perf_counter() - t0
+        err = float(np.abs(W.cpu().numpy() - ref).max() / np.abs(ref).max())
+        cpu = {"value": tc * 1e3, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the whole solve (oracle: numpy/LAPACK zgesv on the same system)", "max_rel_diff_vs_gpu": err}
+    out = {"metric": "tau-domain W~ solve time (Eq. tildeW on the uniform power mesh)", "value": ms, "unit": "ms",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"tau-domain screening: NI={ni} (nk8_nb16 basis), beta={gr.beta}, UPM({p_},{m_}) "
+                                  f"= {npts} points, {N} unknowns x {ni} right-hand sides",
+                      "l2": "system (2 x 20 MB) resident in L2 between pivot steps"},
+           "gpu_launches": int(launches), "roofline_alu": roof, "roofline": None, "cpu_baseline": cpu, "e2e": None}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -236,6 +310,8 @@ def main():
         args.omega = gi.OMEGA_SI
     if args.impl == "reference":
         return run_reference(args, args.config)
+    if args.config == "tau_screen":
+        return run_tau_screen(args)
 
     import torch
     import torch.distributed as dist

@@ -167,6 +167,24 @@ gw_status gw_tau_to_freq_many(gw_ctx* ctx, gw_stat stat, gw_dir dir, int count, 
  * (and grows) on first use. */
 gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, gw_prec prec, double* Wt_iv, int* info);
 
+/* The paper's tau-domain form of Eq. (tildeW) (Sec. III.B.3, after Stan et al.), the
+ * cross-check of the i nu route on small meshes: on a mesh tau_0 = 0 < tau_1 < ... < tau_M = beta
+ * (npts = M + 1, e.g. the uniform power mesh of Sec. III.A) with the trapezoid increments
+ * dtau_r = (tau_{r+1} - tau_{r-1}) / 2 (half the end intervals at r = 0 and M), solves
+ *   sum_r sum_J [delta_IJ delta_pr - v_I P_IJ(tau_p - tau_r) dtau_r] W~_JJ'(tau_r) = v_I P_IJ'(tau_p) v_J'
+ * for W~(tau_r), r = 0..M, v the context's Coulomb diagonal of its iq-th q.
+ * tau [npts]: HOST array, strictly increasing, tau_0 = 0 (else GW_EINVAL).
+ * P_pair cplx [npts][npts][ni][ni] (device): P_pair[p][r] = P(tau_p - tau_r) with the difference
+ * taken modulo beta (bosonic; differences 0 and +-beta give P(0)).
+ * Wt_tau out cplx [npts][ni][ni] (device); info (device int): 0, or k + 1 when elimination
+ * step k found no non-zero pivot (the output is then undefined).
+ * Gauss-Jordan elimination with partial pivoting in FP64 on the (npts ni) x (npts ni + ni)
+ * augmented system, one launch per pivot; workspace 2 (npts ni)(npts ni + ni) 16 bytes, grown
+ * on use. The increments are copied to the device synchronously before the call returns, so
+ * the call cannot be captured into a CUDA graph. */
+gw_status gw_screen_tau(gw_ctx* ctx, int iq, int npts, const double* tau, const double* P_pair, double* Wt_tau,
+                        int* info);
+
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as
  * code whose device memory was handed to another allocator at start-up, or a loop that must

@@ -96,6 +96,8 @@ struct gw_ctx {
   double* d_cpe_N = nullptr;    // real [ngrid][ngrid]: A^T A + lambda^2 I
   double* d_cpe_tab = nullptr;
   void* ff_ws = nullptr;        // float-float copies of a bosonic transform's input
+  void* d_tsys = nullptr;       // gw_screen_tau: two copies of the augmented system + increments
+  size_t tsys_bytes = 0;
   size_t ff_ws_bytes = 0;  // real [1201][ngrid]: Re Phi_m on the QP scan grid
   double* d_cpe_b = nullptr;    // [nprob][ngrid]
   size_t cpe_b_bytes = 0;
