@@ -30,10 +30,16 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
 * screen_tau        -- the paper's tau-domain form of Eq. (tildeW) on the uniform power
                        mesh (Sec. III.B.3); pinned by closed forms of one-mode and
                        exponential polarizations (second and first order in the step).
+* dyson_tau         -- the paper's tau-domain Dyson equation (Eqs. dysongf-dysong) on the
+                       spline-densified uniform mesh; pinned by the closed forms of a static
+                       shift and of a one-pole Sigma^c (first order), the antiperiodic
+                       extension by G0's own definition below zero, and the spline by
+                       scipy's natural spline.
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401
 from . import mlp  # noqa: F401
 from . import screen_tau  # noqa: F401
+from . import dyson_tau  # noqa: F401
 from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
                            cpe_eval, qp_solve, band_gap, pade_resig, cpe_resig, ETA)

@@ -470,3 +470,54 @@ def test_screen_tau_matrix_in_common_eigenbasis():
         errs.append(np.abs(W - Wex).max() / np.abs(Wex).max())
         assert np.abs(W - np.conj(np.swapaxes(W, 1, 2))).max() < 1e-12 * np.abs(W).max()
     assert errs[0] / errs[1] > 3.5 and errs[1] < 5e-3, errs
+
+
+# ------------------------------------------------------------------ tau-domain Dyson (Eqs. dysongf-dysong, Sec. III.B.5)
+def test_dyson_tau_pieces():
+    dt = orc.dyson_tau
+    beta = 20.0
+    tu = gi.upm_grid(beta, 3, 4)
+    t = dt.dense_mesh(tu)
+    h = tu[1] - tu[0]
+    assert np.allclose(np.diff(t), h) and np.isclose(t[-1], beta)
+    assert np.all(np.min(np.abs(tu[:, None] - t[None, :]), axis=1) < 1e-12 * beta)   # the UPM points lie on it
+    # natural spline: through the nodes, exact on linear data, and scipy's natural spline
+    from scipy.interpolate import CubicSpline
+    y = np.sin(tu / 3.0) + 0.1 * tu
+    assert np.allclose(dt.natural_spline(tu, y, tu), y, atol=1e-13)
+    assert np.allclose(dt.natural_spline(tu, 2.0 * tu - 1.0, t), 2.0 * t - 1.0, atol=1e-12)
+    assert np.abs(dt.natural_spline(tu, y, t) - CubicSpline(tu, y, bc_type="natural")(t)).max() < 1e-12
+    # antiperiodic extension of G0 against G0's definition below zero: G0(tau < 0) = e^{-E tau} n_F(E)
+    n = len(t) - 1
+    for E in (0.7, -0.4):
+        F = dt._antiperiodic(dt.g0_tau(E, t, beta), n)
+        d = (np.arange(2 * n + 1) - n) * h
+        nF = 1.0 / (np.exp(beta * E) + 1.0)
+        exact = np.where(d < 0, np.exp(-E * d) * nF, -np.exp(-E * d) * (1.0 - nF))
+        assert np.allclose(F, exact, rtol=1e-12, atol=0)
+
+
+def _dyson_err(model, m, beta=20.0):
+    dt = orc.dyson_tau
+    tu = gi.upm_grid(beta, 3, m)
+    if model == "static":
+        eps, s = 0.4, -0.15
+        G, t = dt.dyson_tau(eps, s, np.zeros(len(tu)), tu)
+        ex = dt.g0_tau(eps + s, t, beta)
+    else:
+        # Sigma^c(i w) = c^2 / (i w - E): G(i w) = 1 / (i w - eps - s - c^2 / (i w - E)) has the two poles
+        # r of (x - eps - s)(x - E) = c^2 with weights (r_i - E) / (r_i - r_j)
+        eps, s, c, E = 0.4, -0.1, 0.3, -0.6
+        G, t = dt.dyson_tau(eps, s, c * c * dt.g0_tau(E, tu, beta), tu)
+        r = np.roots([1.0, -(eps + s + E), (eps + s) * E - c * c])
+        ex = sum(((ri - E) / (ri - rj)) * dt.g0_tau(ri, t, beta) for ri, rj in [(r[0], r[1]), (r[1], r[0])])
+    return np.abs(G - ex).max() / np.abs(ex).max()
+
+
+@pytest.mark.parametrize("model", ["static", "pole"])
+def test_dyson_tau_closed_forms(model):
+    """Static shift: G = G0 at eps + s. One-pole Sigma^c: a two-pole G. The kernels jump at zero
+    difference, so the trapezoid solve converges at first order."""
+    e = [_dyson_err(model, m) for m in (4, 8, 16)]
+    assert all(1.8 < e[i] / e[i + 1] < 2.3 for i in range(2)), e
+    assert e[-1] < 1.5e-2
