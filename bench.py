@@ -286,6 +286,87 @@ def run_tau_screen(args):
     ctx.close()
 
 
+def run_dyson_tau(args):
+    """The paper's tau-domain Dyson equation (gw_dyson_tau) for every state of the benchmarked
+    crystal (Nk = 64, Nb = 64: 4096 states) at beta = 100 on UPM(4, 8) (129 uniform points): one
+    dense 129-unknown solve per state, one block per state. A cross-check of the i w Dyson
+    update, not a step of the benchmarked iteration; timed alone, one GPU."""
+    import torch
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    b.build()
+    cr, gr = gi.make_config("nk64_nb64")
+    beta, p_, m_ = 100.0, 4, 8
+    tu = gi.upm_grid(beta, p_, m_)
+    h = tu[1] - tu[0]
+    n = int(round(beta / h))
+    eps = cr.eps.reshape(-1).copy()
+    nprob = len(eps)
+    rng = np.random.default_rng(20261)
+    s = rng.uniform(-0.2, 0.2, nprob)
+    # synthetic Sigma^c(tau): three poles per state, Sigma^c(i w) = sum c^2 / (i w - E)
+    sig = np.zeros((nprob, len(tu)))
+    for _ in range(3):
+        c2, E = rng.uniform(0.01, 0.1, nprob), rng.uniform(-1.5, 1.5, nprob)
+        x = -np.where(E[:, None] >= 0, np.exp(-np.outer(E, tu)) / (1.0 + np.exp(-beta * E))[:, None],
+                      np.exp(np.outer(E, beta - tu)) / (1.0 + np.exp(beta * E))[:, None])
+        sig += c2[:, None] * x
+    ctx = gw.GW(gr, cr, omega=args.omega, m_mode=2)
+    d_eps, d_s, d_sig = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (eps, s, sig))
+    G = torch.zeros((nprob, n + 1), dtype=torch.float64, device="cuda")
+    info = torch.zeros(nprob, dtype=torch.int32, device="cuda")
+    st = torch.cuda.current_stream()
+    ctx.set_stream(st)
+    for _ in range(args.warmup):
+        ctx.dyson_tau(tu, d_eps, d_s, d_sig, G, info)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    torch.cuda.profiler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.dyson_tau(tu, d_eps, d_s, d_sig, G, info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = ctx.launch_count() - launches0
+    assert int((info != 0).sum().item()) == 0
+    np1 = n + 1
+    # FP64 multiply-adds per state: the Z^c sum (np1^3) and the elimination (sum_k np1 (np1 + 1 - k))
+    fmas = float(np1) ** 3 + float(sum(np1 * (np1 + 1 - k) for k in range(np1)))
+    fp64_tf, _ = gw.measure_alu(0)
+    ach = 2.0 * fmas * nprob / (ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_dyson_tau (one block per state; CUDA events around the call)",
+            "achieved": ach, "peak": fp64_tf, "unit": "TFLOP/s FP64", "frac": ach / fp64_tf,
+            "peak_source": "measured FP64 FMA rate of this GPU (gw_measure_alu, this run)",
+            "flops_per_state": 2.0 * fmas}
+    cpu = None
+    if not args.no_cpu:
+        import time
+
+        import oracle as orc
+        nsamp = 256
+        t0 = time.perf_counter()
+        ref = np.stack([orc.dyson_tau.dyson_tau(eps[i], s[i], sig[i], tu)[0] for i in range(nsamp)])
+        tc = time.perf_counter() - t0
+        err = float(np.abs(G[:nsamp].cpu().numpy() - ref).max() / np.abs(ref).max())
+        cpu = {"value": tc * 1e3 * nprob / nsamp, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"the first {nsamp} of the {nprob} states (numpy/LAPACK), scaled to all states",
+               "max_rel_diff_vs_gpu": err}
+    out = {"metric": "tau-domain Dyson solve time, all states (Eqs. dysongf-dysong)", "value": ms, "unit": "ms",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"tau-domain Dyson: {nprob} states (nk64_nb64 band energies), beta={beta}, "
+                                  f"Sigma^c on UPM({p_},{m_}) = {len(tu)} points, spline to {np1} uniform points",
+                      "l2": "per-state systems (133 KB each) written and solved by one block"},
+           "gpu_launches": int(launches), "roofline_alu": roof, "roofline": None, "cpu_baseline": cpu, "e2e": None}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,6 +393,8 @@ def main():
         return run_reference(args, args.config)
     if args.config == "tau_screen":
         return run_tau_screen(args)
+    if args.config == "dyson_tau":
+        return run_dyson_tau(args)
 
     import torch
     import torch.distributed as dist

@@ -185,6 +185,25 @@ gw_status gw_screen(gw_ctx* ctx, int iq0, int nqb, const double* P_iv, gw_prec p
 gw_status gw_screen_tau(gw_ctx* ctx, int iq, int npts, const double* tau, const double* P_pair, double* Wt_tau,
                         int* info);
 
+/* The paper's tau-domain Dyson equation for the diagonal G (Sec. III.B.5, Eqs. dysongf, zxjk,
+ * zcjk, dysong), the check of the i w update of gw_green_tau on small meshes. For each of nprob
+ * states, Sigma^c given on a mesh tau_upm (HOST array of n_upm points, tau_0 = 0, last point
+ * beta, every point a multiple of h = tau_1 - tau_0, as on the uniform power mesh) is carried
+ * by a natural cubic spline to the uniform mesh t_i = i h, i = 0..n (n = beta / h), where
+ *   sum_r [delta_pr - w_r Z(t_p, t_r)] G(t_r) = G0(t_p),
+ *   Z(t, t2) = G0(t - t2) s + sum_l w_l G0(t - t_l) Sigma^c(t_l - t2),
+ * w the trapezoid increments (h, h/2 at both ends); G0(tau) = -e^{-eps tau}(1 - n_F(eps)) and
+ * Sigma^c are antiperiodic (f(d) = -f(d + beta) for d < 0; a zero difference takes the value
+ * at 0+). eps, s [nprob] (device; s = Sigma^x + Sigma^H - Sigma_0 of the state);
+ * sigc [nprob][n_upm] (device); G out [nprob][n + 1] (device, on the uniform mesh);
+ * info [nprob] (device): 0, or k + 1 for a zero pivot at elimination step k (that state's G
+ * is then not written). GW_EINVAL unless 3 <= n_upm <= 1024 and n + 1 <= 1024 and the mesh
+ * is as described. FP64; one block per state (Gauss-Jordan with partial pivoting); workspace
+ * (n + 1)(n + 2) 8 bytes per state, for chunks of states of at most 1 GiB. The mesh is copied
+ * to the device synchronously before the call returns (not capturable in a CUDA graph). */
+gw_status gw_dyson_tau(gw_ctx* ctx, int64_t nprob, int n_upm, const double* tau_upm, const double* eps,
+                       const double* s, const double* sigc, double* G, int* info);
+
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as
  * code whose device memory was handed to another allocator at start-up, or a loop that must
