@@ -6,6 +6,7 @@
 // ties to even) and give, on their fast path, exactly what the conversion instruction gives:
 //   d2f(x)        = RN_float(x)
 //   d2ff(x, h, l) : h = RN_float(x), l = RN_float(x - h)   (x - h is exact in double)
+//   f2d(x)        = x widened to double (exact)
 // Fast path: 2^-74 <= |x| < 2^127 for d2ff, 2^-126 <= |x| < 2^127 for d2f (both words then
 // normal floats); every other value (zero, subnormals, overflow, inf, nan) takes the
 // conversion instructions. The host build (plain C++) runs the same integer logic and serves
@@ -42,6 +43,28 @@ GW_HD float fbits(uint32_t u) {
   return f;
 #endif
 }
+
+GW_HD uint32_t ubits(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  std::memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+
+GW_HD double dfrom(uint64_t u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  double d;
+  std::memcpy(&d, &u, sizeof d);
+  return d;
+#endif
+}
+
+GW_HD double f2d_hw(float x) { return (double)x; }
 
 GW_HD float i2f_rn(int32_t r) {
 #if defined(__CUDA_ARCH__)
@@ -95,6 +118,15 @@ GW_HD void d2ff(double x, float& h, float& l) {
   // x - h = r 2^(E - 1075): RN of the integer, then an exact scaling by a power of two
   // (the product is a normal float since |r| >= 1 and E >= 949)
   l = i2f_rn(r) * fbits((E - 948u) << 23);
+}
+
+// float -> double, exact: the exponent re-biased (127 -> 1023) and the significand widened, for
+// every normal float; zeros, subnormals, infinities and nan take the conversion instruction.
+GW_HD double f2d(float x) {
+  const uint32_t u = ubits(x);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return f2d_hw(x);
+  return dfrom(((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29));
 }
 
 }  // namespace cvt

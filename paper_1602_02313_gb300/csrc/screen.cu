@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 #include <string>
 
 #include "arith.cuh"
@@ -116,9 +117,11 @@ __global__ void __launch_bounds__(512) k_screen(const double2* __restrict__ P, c
 // shared memory. The rank-32 updates are register-tiled (8 rows x 4 columns per thread), so
 // the matrix is read and written once per block row, for any ni that is a multiple of 32.
 //
-// The arithmetic is a policy (arith.cuh): native FP64, or float-float on the FP32 pipes.
+// The arithmetic is a policy (arith.cuh): native FP64, float-float on the FP32 pipes, or plain
+// FP32 (whose scaling by v^1/2 on the way in and out also stays in FP32).
 constexpr int GJ_B = 32;
 constexpr int GJ_RP = 256;  // rows per update pass (the shared-memory panel)
+constexpr int kScreenMaxNi = 1024;  // the largest basis a context accepts
 
 using arith::Fp64;
 using arith::Ff32;
@@ -142,12 +145,26 @@ __global__ void __launch_bounds__(256, AR::kBlocksPerSm) k_screen_inv(const doub
   const double2* Ps = P + (size_t)sys * ni * ni;
   S* A = work + (size_t)sys * ni * ni;
   const int t = threadIdx.x;
+  constexpr bool kF32 = std::is_same<AR, F32>::value;
+  __shared__ float svf[kF32 ? kScreenMaxNi : 1];  // FP32: v^1/2 as floats
   if (t == 0) bad = 0;
-  for (int e = t; e < ni * ni; e += blockDim.x) {
-    const int I = e / ni, J = e % ni;
-    const double s = sv[I] * sv[J];
-    const double2 p = Ps[e];
-    A[e] = AR::from((I == J ? 1.0 : 0.0) - s * p.x, -s * p.y);
+  if constexpr (kF32) {
+    // A = 1 - Pi entirely in FP32 (integer-pipe conversions of the inputs; no FP64 operations)
+    for (int I = t; I < ni; I += blockDim.x) svf[I] = cvt::d2f(sv[I]);
+    __syncthreads();
+    for (int e = t; e < ni * ni; e += blockDim.x) {
+      const int I = e / ni, J = e % ni;
+      const float s = svf[I] * svf[J];
+      const double2 p = Ps[e];
+      A[e] = make_float2((I == J ? 1.f : 0.f) - s * cvt::d2f(p.x), -s * cvt::d2f(p.y));
+    }
+  } else {
+    for (int e = t; e < ni * ni; e += blockDim.x) {
+      const int I = e / ni, J = e % ni;
+      const double s = sv[I] * sv[J];
+      const double2 p = Ps[e];
+      A[e] = AR::from((I == J ? 1.0 : 0.0) - s * p.x, -s * p.y);
+    }
   }
   __syncthreads();
   const int tr = t & 31, tc = t >> 5;  // row lane, column group (8 groups x 4 columns)
@@ -165,8 +182,10 @@ __global__ void __launch_bounds__(256, AR::kBlocksPerSm) k_screen_inv(const doub
         if (t == 0) bad = k0 + j + 1;
         break;
       }
-      const S ip = AR::inv(p);
       if (t < GJ_B) {
+        // one warp: the reciprocal is ~40 FP64-pipe instructions for the FP32-based policies,
+        // and only these threads use it
+        const S ip = AR::inv(p);
         fcol[t] = Pinv[t * (GJ_B + 1) + j];
         if (t == j) {
           rowj[t] = ip;
@@ -281,11 +300,20 @@ __global__ void __launch_bounds__(256, AR::kBlocksPerSm) k_screen_inv(const doub
   }
   // W~ = v^1/2 (A^-1 - 1) v^1/2
   double2* Ws = W + (size_t)sys * ni * ni;
-  for (int e = t; e < ni * ni; e += blockDim.x) {
-    const int I = e / ni, J = e % ni;
-    const double s = sv[I] * sv[J];
-    const double2 x = AR::to(A[e]);
-    Ws[e] = make_double2(s * (x.x - (I == J ? 1.0 : 0.0)), s * x.y);
+  if constexpr (kF32) {
+    for (int e = t; e < ni * ni; e += blockDim.x) {
+      const int I = e / ni, J = e % ni;
+      const float s = svf[I] * svf[J];
+      const float2 x = A[e];
+      Ws[e] = make_double2(cvt::f2d(s * (x.x - (I == J ? 1.f : 0.f))), cvt::f2d(s * x.y));
+    }
+  } else {
+    for (int e = t; e < ni * ni; e += blockDim.x) {
+      const int I = e / ni, J = e % ni;
+      const double s = sv[I] * sv[J];
+      const double2 x = AR::to(A[e]);
+      Ws[e] = make_double2(s * (x.x - (I == J ? 1.0 : 0.0)), s * x.y);
+    }
   }
   if (t == 0) info[sys] = 0;
 }

@@ -65,6 +65,19 @@ int main() {
   // values of the workload's magnitudes
   std::normal_distribution<double> nd(0.0, 1.0);
   for (int i = 0; i < 1000000; ++i) check(nd(rng) * std::pow(10.0, (double)(i % 17) - 8.0));
+  // float -> double widening, bit for bit against the host's conversion, every float exponent
+  for (uint32_t e = 0; e < 256; ++e)
+    for (int i = 0; i < 4000; ++i) {
+      const uint32_t u = ((uint32_t)(rng() & 1) << 31) | (e << 23) | (uint32_t)(rng() & 0x7FFFFFu);
+      float f;
+      std::memcpy(&f, &u, sizeof f);
+      const double a = gwi::cvt::f2d(f), b = (double)f;
+      ++n_checked;
+      uint64_t ua, ub;
+      std::memcpy(&ua, &a, sizeof ua);
+      std::memcpy(&ub, &b, sizeof ub);
+      if (!(ua == ub || (std::isnan(a) && std::isnan(b))) && n_bad++ < 10) std::printf("f2d mismatch %a\n", (double)f);
+    }
   std::printf("checked %ld values, %ld mismatches\n", n_checked, n_bad);
   return n_bad ? 1 : 0;
 }
