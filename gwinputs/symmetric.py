@@ -129,3 +129,27 @@ def _fill(ops, kimg, pi, bases, v, eps, kmq, n, nk, nb, nocc, ni, beta, rng):
     c.ibz, c.reps, c.pi = ibz, reps, pi
     c.seed = 0
     return c
+
+
+def restrict_q(c, qs):
+    """The crystal seen by a context that holds only the q points qs (e.g. the irreducible
+    ones): v, k - q rows and M of those q; seed 0 (M is passed explicitly)."""
+    import copy
+    r = copy.copy(c)
+    qs = list(qs)
+    r.nq = len(qs)
+    r.v = np.ascontiguousarray(c.v[qs])
+    r.kmq = np.ascontiguousarray(c.kmq[qs])
+    r.M = np.ascontiguousarray(c.M[qs])
+    r.qlist = qs
+    return r
+
+
+def star_kinv(c, q):
+    """For each member R q of q's star (c.reps[q]): the index of R^-1 k for every k, [nrep][nk]."""
+    out = []
+    for r in c.reps[q]:
+        inv = np.empty(c.nk, np.int32)
+        inv[c.kimg[r]] = np.arange(c.nk, dtype=np.int32)
+        out.append(inv)
+    return np.array(out, np.int32)

@@ -204,6 +204,15 @@ gw_status gw_screen_tau(gw_ctx* ctx, int iq, int npts, const double* tau, const 
 gw_status gw_dyson_tau(gw_ctx* ctx, int64_t nprob, int n_upm, const double* tau_upm, const double* eps,
                        const double* s, const double* sigc, double* G, int* info);
 
+/* Crystal-symmetry reduction (Sec. III.C): the contribution of q' = R q to Sigma_n(k) equals the
+ * contribution of q at R^-1 k, so a caller that computes P, W~ and gw_selfenergy for the
+ * irreducible q points only, each into a zeroed buffer T, carries each one to its star with
+ *   S[k][c] += sum_{r < nrep} T[kinv[r][k]][c],   c < ncol,
+ * kinv [nrep][nk] (device int): index of R_r^-1 k on the mesh, one row per member R_r q of the
+ * star; T, S [nk][ncol] (device; ncol = nb ntau for Sigma^c, nb for Sigma^x). Entries of kinv
+ * outside [0, nk) are skipped. GW_EINVAL for nrep < 1 or ncol < 1. */
+gw_status gw_sigma_star(gw_ctx* ctx, int nrep, const int* kinv, int64_t ncol, const double* T, double* S);
+
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as
  * code whose device memory was handed to another allocator at start-up, or a loop that must

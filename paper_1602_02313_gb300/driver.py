@@ -39,7 +39,7 @@ class Chain:
     """Buffers and call sequence of one GW iteration on a libgw context."""
 
     def __init__(self, ctx, eps, prec=GW_FP16X2, qb=8, iqs=None, cont_method=GW_PADE, cpe_ridge=1e-3, mlp=None,
-                 nfit=64, screen_prec=None, keep_w=False):
+                 nfit=64, screen_prec=None, keep_w=False, star=None):
         self.ctx = ctx
         g, cr = ctx.grid, ctx.cr
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
@@ -51,6 +51,10 @@ class Chain:
         if screen_prec is None:
             screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32
         self.screen_prec = screen_prec
+        # crystal symmetry (Sec. III.C): iqs are the irreducible q points and star[j] the
+        # device int32 [nrep][nk] map k -> R^-1 k of each member of iqs[j]'s star; every q's
+        # self-energy goes to T buffers first and is carried to its star (gw_sigma_star)
+        self.star = star
         self.bose_prec = GW_FP64 if screen_prec == GW_FP64 else GW_F32X2
         self.iqs = list(range(cr.nq)) if iqs is None else list(iqs)
         self.qb = max(1, min(qb, len(self.iqs)))
@@ -63,6 +67,9 @@ class Chain:
         self.occ = torch.zeros(nk, nb, dtype=f8, **d)
         self.S = torch.zeros(nk, nb, nt, dtype=f8, **d)
         self.Sx = torch.zeros(nk, nb, dtype=f8, **d)
+        if star is not None:
+            self.Tc = torch.zeros(nk, nb, nt, dtype=f8, **d)
+            self.Tx = torch.zeros(nk, nb, dtype=f8, **d)
         self.P = torch.zeros(self.qb, nt, ni, ni, dtype=c16, **d)
         self.Piv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
         self.Wiv = torch.zeros(self.qb, self.nnu, ni, ni, dtype=c16, **d)
@@ -128,14 +135,25 @@ class Chain:
             for j, iq in enumerate(batch):
                 if self.Wkeep is not None:
                     self.Wkeep[b0 + j].copy_(self.Wt[j])
-                self._timed("selfenergy", lambda: ctx.selfenergy(iq, G, occ, self.Wt[j], self.S, self.Sx, self.prec))
+                self._timed("selfenergy", lambda: self._sigma_q(b0 + j, iq, G, occ, self.Wt[j]))
 
     def sigma_fixed_w(self, G, occ):
         """Sigma^c(tau), Sigma^x from G with the W~(tau) kept by the first pass (GW0)."""
         self.S.zero_()
         self.Sx.zero_()
         for j, iq in enumerate(self.iqs):
-            self.ctx.selfenergy(iq, G, occ, self.Wkeep[j], self.S, self.Sx, self.prec)
+            self._sigma_q(j, iq, G, occ, self.Wkeep[j])
+
+    def _sigma_q(self, pos, iq, G, occ, Wt):
+        """Sigma^c, Sigma^x += the contribution of q (and of its star, with symmetry)."""
+        if self.star is None:
+            self.ctx.selfenergy(iq, G, occ, Wt, self.S, self.Sx, self.prec)
+            return
+        self.Tc.zero_()
+        self.Tx.zero_()
+        self.ctx.selfenergy(iq, G, occ, Wt, self.Tc, self.Tx, self.prec)
+        self.ctx.sigma_star(self.star[pos], self.Tc, self.S)
+        self.ctx.sigma_star(self.star[pos], self.Tx, self.Sx)
 
     def finish(self, vxc=None):
         """Sigma(i w), Dyson update, continuation and QP energies from the summed Sigma."""
