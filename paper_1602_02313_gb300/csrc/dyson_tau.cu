@@ -46,6 +46,8 @@ __global__ void __launch_bounds__(kDyThreads) k_dyson_tau(int nu, const double* 
   double* g0 = sy + nu;        // [n + 1] G0 on the uniform mesh
   double* sc = g0 + n + 1;     // [n + 1] Sigma^c on the uniform mesh
   double* fc = sc + n + 1;     // [n + 1] column factors of an elimination step
+  double* gf = fc + n + 1;     // [2 n + 1] G0(d h), d = -n..n (antiperiodic extension), at gf[d + n]
+  double* sf = gf + 2 * n + 1; // [2 n + 1] Sigma^c(d h) likewise
   __shared__ double rv[kDyThreads];
   __shared__ int ri[kDyThreads];
   __shared__ int bad;
@@ -91,16 +93,22 @@ __global__ void __launch_bounds__(kDyThreads) k_dyson_tau(int nu, const double* 
     g0[i] = g0_at(e, ti, beta);
   }
   __syncthreads();
-  // [I - Z diag(w) | G0]
+  for (int d = t; d <= 2 * n; d += kDyThreads) {
+    gf[d] = anti(g0, d - n, n);
+    sf[d] = anti(sc, d - n, n);
+  }
+  __syncthreads();
+  // [I - Z diag(w) | G0]; the trapezoid sum over l as h (sum of all terms - half the two end
+  // terms), one multiply-add per term
   for (int idx = t; idx < np1 * np1; idx += kDyThreads) {
     const int p = idx / np1, r = idx % np1;
+    const double* gp = gf + p + n;  // gp[-l] = G0(t_p - t_l)
+    const double* sr = sf + n - r;  // sr[l] = Sigma^c(t_l - t_r)
     double zc = 0.0;
-    for (int l = 0; l <= n; ++l) {
-      const double wl = (l == 0 || l == n) ? 0.5 * h : h;
-      zc = fma(wl * anti(g0, p - l, n), anti(sc, l - r, n), zc);
-    }
+    for (int l = 0; l <= n; ++l) zc = fma(gp[-l], sr[l], zc);
+    zc = h * (zc - 0.5 * (gp[0] * sr[0] + gp[-n] * sr[n]));
     const double wr = (r == 0 || r == n) ? 0.5 * h : h;
-    const double z = anti(g0, p - r, n) * s + zc;
+    const double z = gp[-r] * s + zc;
     A[(size_t)p * L + r] = (p == r ? 1.0 : 0.0) - wr * z;
   }
   for (int p = t; p < np1; p += kDyThreads) A[(size_t)p * L + np1] = g0[p];
@@ -192,7 +200,7 @@ extern "C" gw_status gw_dyson_tau(gw_ctx* c, int64_t nprob, int n_upm, const dou
   // the nodes are copied before the call returns
   if (cudaMemcpy(xu, tau_upm, n_upm * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return set_err(c, GW_ECUDA, "gw_dyson_tau: copy of the mesh");
-  const size_t smem = (3 * (size_t)n_upm + 3 * (size_t)(n + 1)) * sizeof(double);
+  const size_t smem = (3 * (size_t)n_upm + 3 * (size_t)(n + 1) + 2 * (size_t)(2 * n + 1)) * sizeof(double);
   cudaFuncSetAttribute(k_dyson_tau, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   kt_begin(c, "dyson_tau");
   for (int64_t b0 = 0; b0 < nprob; b0 += chunk) {
