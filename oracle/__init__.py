@@ -35,11 +35,15 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                        shift and of a one-pole Sigma^c (first order), the antiperiodic
                        extension by G0's own definition below zero, and the spline by
                        scipy's natural spline.
+* offdiag           -- the full band matrix of Sigma^c and Sigma^x (Eqs. sigc, sigx without
+                       the diagonal approximation); pinned by its diagonal (oracle.selfenergy),
+                       Hermiticity and covariance under a unitary change of bands.
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401
 from . import mlp  # noqa: F401
 from . import screen_tau  # noqa: F401
 from . import dyson_tau  # noqa: F401
+from . import offdiag  # noqa: F401
 from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
                            cpe_eval, qp_solve, band_gap, pade_resig, cpe_resig, ETA)

@@ -521,3 +521,26 @@ def test_dyson_tau_closed_forms(model):
     e = [_dyson_err(model, m) for m in (4, 8, 16)]
     assert all(1.8 < e[i] / e[i + 1] < 2.3 for i in range(2)), e
     assert e[-1] < 1.5e-2
+
+
+# ------------------------------------------------------------------ off-diagonal self-energy (Eqs. sigc, sigx, full band matrix)
+def test_offdiag_selfenergy_pins():
+    from oracle import offdiag as od
+    cr, gr = gi.make_config("nk8_nb16")
+    rng = np.random.default_rng(41)
+    M = gi.m_for_q(cr, 0)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    X = rng.standard_normal((gr.ntau, cr.ni, cr.ni)) + 1j * rng.standard_normal((gr.ntau, cr.ni, cr.ni))
+    W = -(X @ np.conj(np.swapaxes(X, 1, 2))) / cr.ni                  # Hermitian, like W~(tau)
+    Sc, Sx = od.selfenergy_offdiag(M, G, W, cr.v[0], cr.kmq[0], occ, omega=1.3)
+    sc, sx, _ = orc.selfenergy(M, G, W, cr.v[0], cr.kmq[0], occ, omega=1.3)
+    d = np.arange(cr.nb)
+    assert np.allclose(Sc[:, d, d, :].real, sc, rtol=0, atol=1e-12 * np.abs(sc).max())   # the diagonal
+    assert np.allclose(Sx[:, d, d].real, sx, rtol=0, atol=1e-12 * np.abs(sx).max())
+    assert np.abs(Sc - np.conj(np.swapaxes(Sc, 1, 2))).max() < 1e-12 * np.abs(Sc).max()  # Hermitian
+    assert np.abs(Sx - np.conj(np.swapaxes(Sx, 1, 2))).max() < 1e-12 * np.abs(Sx).max()
+    # a unitary change of the k-side bands, M -> M U, gives Sigma -> U^+ Sigma U
+    U, _ = np.linalg.qr(rng.standard_normal((cr.nb, cr.nb)) + 1j * rng.standard_normal((cr.nb, cr.nb)))
+    Sc2, Sx2 = od.selfenergy_offdiag(M @ U, G, W, cr.v[0], cr.kmq[0], occ, omega=1.3)
+    assert np.abs(Sc2 - np.einsum("an,kabt,bm->knmt", U.conj(), Sc, U)).max() < 1e-12 * np.abs(Sc).max()
+    assert np.abs(Sx2 - np.einsum("an,kab,bm->knm", U.conj(), Sx, U)).max() < 1e-12 * np.abs(Sx).max()
