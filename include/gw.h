@@ -213,6 +213,16 @@ gw_status gw_dyson_tau(gw_ctx* ctx, int64_t nprob, int n_upm, const double* tau_
  * outside [0, nk) are skipped. GW_EINVAL for nrep < 1 or ncol < 1. */
 gw_status gw_sigma_star(gw_ctx* ctx, int nrep, const int* kinv, int64_t ncol, const double* T, double* S);
 
+/* Off-diagonal self-energy of the iq-th q in the band basis (Eqs. sigc and sigx without the
+ * diagonal approximation of Sec. III.B), ACCUMULATED:
+ *   Sigma^c_nm(k|tau) += -1/(Omega N_k) sum_j G_j(k-q|tau) sum_IJ conj(M^I_jn) W~_IJ(tau) M^J_jm,
+ *   Sigma^x_nm(k)     += -1/(Omega N_k) sum_j occ_j(k-q) sum_I v_I conj(M^I_jn) M^I_jm.
+ * G_tau [nk][nb][ntau], occ [nk][nb] (may be NULL when Sx is), Wt_tau cplx [ntau][ni][ni];
+ * S_tau cplx [nk][nb][nb][ntau]; Sx cplx [nk][nb][nb] (may be NULL). FP64 on the CUDA cores;
+ * GW_EINVAL when (ni nb + nb^2) 16 bytes exceed 200 KiB (one (k, tau)'s working set). */
+gw_status gw_selfenergy_offdiag(gw_ctx* ctx, int iq, const double* G_tau, const double* occ, const double* Wt_tau,
+                                double* S_tau, double* Sx);
+
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as
  * code whose device memory was handed to another allocator at start-up, or a loop that must

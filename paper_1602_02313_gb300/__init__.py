@@ -32,7 +32,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 
 # Every symbol declared in include/gw.h.
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
-           "gw_tau_to_freq", "gw_tau_to_freq_many", "gw_screen", "gw_screen_tau", "gw_dyson_tau", "gw_sigma_star", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
+           "gw_tau_to_freq", "gw_tau_to_freq_many", "gw_screen", "gw_screen_tau", "gw_dyson_tau", "gw_sigma_star", "gw_selfenergy_offdiag", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
            "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning", "gw_measure_alu",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
@@ -116,6 +116,7 @@ def load_library(path=LIB_PATH):
         "gw_screen_tau": [vp, i32, i32, vp, vp, vp, vp],
         "gw_dyson_tau": [vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "gw_sigma_star": [vp, i32, vp, i64, vp, vp],
+        "gw_selfenergy_offdiag": [vp, i32, vp, vp, vp, vp, vp],
         "gw_screen": [vp, i32, i32, vp, i32, vp, vp],
         "gw_selfenergy": [vp, i32, vp, vp, vp, i32, vp, vp],
         "gw_continue": [vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp],
@@ -278,6 +279,11 @@ class GW:
         """kinv: device int32 [nrep][nk]; T, S: device float64 [nk][...] (S accumulated)."""
         self._check(self.lib.gw_sigma_star(self.h, int(kinv.shape[0]), _ptr(kinv), int(T.numel() // T.shape[0]),
                                            _ptr(T), _ptr(S)), "gw_sigma_star")
+
+    def selfenergy_offdiag(self, iq, G, occ, W, S, Sx=None):
+        """S: complex128 [nk][nb][nb][ntau], Sx: complex128 [nk][nb][nb] or None (both accumulated)."""
+        self._check(self.lib.gw_selfenergy_offdiag(self.h, int(iq), _ptr(G), _ptr(occ), _ptr(W), _ptr(S), _ptr(Sx)),
+                    "gw_selfenergy_offdiag")
 
     def screen(self, iq0, nqb, P_iv, W_iv, info, prec=GW_FP64):
         self._check(self.lib.gw_screen(self.h, iq0, nqb, _ptr(P_iv), int(prec), _ptr(W_iv), _ptr(info)), "gw_screen")
