@@ -420,6 +420,54 @@ def run_sym(args, prec):
     print(json.dumps(out))
 
 
+def run_offdiag(args):
+    """Off-diagonal self-energy (gw_selfenergy_offdiag, FP64) of one q of a synthetic crystal with
+    Nk = 64, Nb = 32, NI = 128, Ntau = 32; timed alone against the measured FP64 rate."""
+    import torch
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    b.build()
+    cr = gi.make_crystal(seed=2101, nk=64, nb=32, nocc=16, ni=128, beta=100.0, qlist=[5])
+    gr = gi.make_grid(100.0, 32, 32, 32, ncont=64)
+    ctx = gw.GW(gr, cr, omega=args.omega)
+    rng = np.random.default_rng(2102)
+    X = rng.standard_normal((gr.ntau, cr.ni, cr.ni)) + 1j * rng.standard_normal((gr.ntau, cr.ni, cr.ni))
+    W = torch.from_numpy(-(X @ np.conj(np.swapaxes(X, 1, 2))) / cr.ni).cuda()
+    G = torch.from_numpy(np.ascontiguousarray(np.repeat(-np.exp(-np.abs(cr.eps))[:, :, None], gr.ntau, 2))).cuda()
+    occ = torch.from_numpy((cr.eps < 0).astype(np.float64)).cuda()
+    S = torch.zeros((cr.nk, cr.nb, cr.nb, gr.ntau), dtype=torch.complex128, device="cuda")
+    Sx = torch.zeros((cr.nk, cr.nb, cr.nb), dtype=torch.complex128, device="cuda")
+    st = torch.cuda.current_stream()
+    ctx.set_stream(st)
+    for _ in range(args.warmup):
+        ctx.selfenergy_offdiag(0, G, occ, W, S, Sx)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        ctx.selfenergy_offdiag(0, G, occ, W, S, Sx)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    nk, nb, ni, nt = cr.nk, cr.nb, cr.ni, gr.ntau
+    macs = float(nk) * nt * nb * (ni * ni * nb + ni * nb * nb) + float(nk) * nb ** 3 * ni
+    fp64_tf, _ = gw.measure_alu(0)
+    ach = 8.0 * macs / (ms * 1e-3) / 1e12
+    out = {"metric": "off-diagonal self-energy time, one q (Eqs. sigc, sigx as band matrices)", "value": ms,
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"one q: Nk={nk}, Nb={nb}, NI={ni}, Ntau={nt}"},
+           "gpu_launches": 2 * args.steps,
+           "roofline_alu": {"bound": "alu", "kernel": "k_sigma_offdiag + k_sigx_offdiag", "achieved": ach,
+                            "peak": fp64_tf, "unit": "TFLOP/s FP64", "frac": ach / fp64_tf,
+                            "peak_source": "measured FP64 FMA rate of this GPU (gw_measure_alu, this run)"},
+           "roofline": None, "cpu_baseline": None, "e2e": None}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,6 +496,8 @@ def main():
         return run_tau_screen(args)
     if args.config == "dyson_tau":
         return run_dyson_tau(args)
+    if args.config == "offdiag":
+        return run_offdiag(args)
     if args.config == "sym":
         import paper_1602_02313_gb300 as gw
         return run_sym(args, gw.PREC[args.prec])
