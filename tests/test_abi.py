@@ -78,3 +78,7 @@ def test_invalid_arguments_rejected_on_host(gw):
     assert lib.gw_kernel_timing(None, 1) == gw.GW_EINVAL
     assert lib.gw_measure_alu(0, None, None) == gw.GW_EINVAL
     assert lib.gw_tau_to_freq_many(None, gw.GW_BOSE, gw.GW_TAU_TO_IW, 1, 1, None, gw.GW_FP64, None) == gw.GW_EINVAL
+    assert lib.gw_screen_tau(None, 0, 3, None, None, None, None) == gw.GW_EINVAL
+    assert lib.gw_dyson_tau(None, 1, 4, None, None, None, None, None, None) == gw.GW_EINVAL
+    assert lib.gw_sigma_star(None, 1, None, 1, None, None) == gw.GW_EINVAL
+    assert lib.gw_selfenergy_offdiag(None, 0, None, None, None, None, None) == gw.GW_EINVAL
