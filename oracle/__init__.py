@@ -37,7 +37,9 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                        scipy's natural spline.
 * offdiag           -- the full band matrix of Sigma^c and Sigma^x (Eqs. sigc, sigx without
                        the diagonal approximation); pinned by its diagonal (oracle.selfenergy),
-                       Hermiticity and covariance under a unitary change of bands.
+                       Hermiticity and covariance under a unitary change of bands. Its matrix
+                       Dyson update (dyson_matrix_iw) is pinned by the downfolding closed form
+                       of a pole self-energy, its diagonal reduction and unitary covariance.
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401

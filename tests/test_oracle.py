@@ -544,3 +544,65 @@ def test_offdiag_selfenergy_pins():
     Sc2, Sx2 = od.selfenergy_offdiag(M @ U, G, W, cr.v[0], cr.kmq[0], occ, omega=1.3)
     assert np.abs(Sc2 - np.einsum("an,kabt,bm->knmt", U.conj(), Sc, U)).max() < 1e-12 * np.abs(Sc).max()
     assert np.abs(Sx2 - np.einsum("an,kab,bm->knm", U.conj(), Sx, U)).max() < 1e-12 * np.abs(Sx).max()
+
+
+def _matrix_dyson_case(nt, seed=7, nb=6, na=3):
+    from oracle import offdiag as od
+    gr = gi.make_grid(20.0, nt, nt, nt, ncont=64)
+    rng = np.random.default_rng(seed)
+    w = (2 * np.asarray(gr.w_idx) + 1) * np.pi / gr.beta
+    eps = np.sort(rng.uniform(-1, 1, (1, nb)), 1)
+
+    def herm(s):
+        X = rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb))
+        return s * (X + X.conj().T) / 2
+
+    Sx, Vx = herm(0.1)[None], herm(0.05)[None]
+    E = rng.uniform(-1.5, 1.5, na)
+    C = 0.2 * (rng.standard_normal((nb, na)) + 1j * rng.standard_normal((nb, na)))
+    Sc = np.einsum("na,aw,ma->nmw", C, 1.0 / (1j * w[None, :] - E[:, None]), C.conj())[None]
+    G, occ = od.dyson_matrix_iw(eps, Sx, Vx, Sc, gr)
+    # downfolding: Sigma^c(i w) = C (i w - E)^-1 C^+ makes G the system block of the enlarged
+    # Hermitian problem [[H~, C], [C^+, diag(E)]], whose tau form is exact by eigendecomposition
+    Hb = np.zeros((nb + na, nb + na), complex)
+    Hb[:nb, :nb] = np.diag(eps[0]) + Sx[0] - Vx[0]
+    Hb[:nb, nb:], Hb[nb:, :nb], Hb[nb:, nb:] = C, C.conj().T, np.diag(E)
+    lam, U = np.linalg.eigh(Hb)
+    g0, f0 = orc.green_tau0(lam[None, :], gr.tau, gr.beta)
+    Gex = np.einsum("na,at,ma->nmt", U[:nb], g0[0], U[:nb].conj())
+    occx = (U[:nb] * f0[0][None, :]) @ U[:nb].conj().T
+    return gr, (eps, Sx, Vx, Sc), G, occ, Gex, occx
+
+
+def test_matrix_dyson_pins():
+    from oracle import offdiag as od
+    errs = []
+    for nt in (48, 64):
+        gr, args, G, occ, Gex, occx = _matrix_dyson_case(nt)
+        errs.append(np.abs(G[0] - Gex).max() / np.abs(Gex).max())
+        assert np.abs(G - np.conj(np.swapaxes(G, 1, 2))).max() < 1e-12 * np.abs(G).max()   # Hermitian
+    assert errs[1] < 1e-5 and errs[0] > errs[1], errs          # the sparse-grid transform converges
+    assert np.abs(occ[0] - occx).max() < 5e-5                  # G(beta^-) from the same transform
+    # a unitary change of bands: every matrix -> U^+ X U gives G -> U^+ G U
+    eps, Sx, Vx, Sc = args
+    nb = eps.shape[1]
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((nb, nb)) + 1j * rng.standard_normal((nb, nb)))
+    H = np.diag(eps[0]) + Sx[0] - Vx[0]
+    G2, _ = od.dyson_matrix_iw(np.zeros((1, nb)), (U.conj().T @ H @ U)[None], np.zeros((1, nb, nb)),
+                               np.einsum("an,kabw,bm->knmw", U.conj(), Sc, U), gr)
+    assert np.abs(G2 - np.einsum("an,kabt,bm->knmt", U.conj(), G, U)).max() < 1e-12 * np.abs(G).max()
+    # diagonal matrices reduce to the diagonal Dyson oracle
+    cr, grd = gi.make_config("nk8_nb16")
+    w = (2 * np.asarray(grd.w_idx) + 1) * np.pi / grd.beta
+    r = np.random.default_rng(1)
+    sx, vx = r.uniform(-0.2, 0.2, (cr.nk, cr.nb)), r.uniform(-0.1, 0.1, (cr.nk, cr.nb))
+    sc = (r.uniform(0.05, 0.2, (cr.nk, cr.nb)) ** 2)[..., None] / (1j * w - r.uniform(-1, 1, (cr.nk, cr.nb))[..., None])
+    Gd, occd = orc.dyson_iw(cr.eps, sx, vx, sc, grd)
+    d = np.arange(cr.nb)
+    M3 = lambda x: np.einsum("kn,nm->knm", x, np.eye(cr.nb)).astype(complex)  # noqa: E731
+    Sm = np.zeros((cr.nk, cr.nb, cr.nb, len(w)), complex)
+    Sm[:, d, d, :] = sc
+    Gm, occm = od.dyson_matrix_iw(cr.eps, M3(sx), M3(vx), Sm, grd)
+    assert np.abs(Gm[:, d, d, :] - Gd).max() < 1e-13 * np.abs(Gd).max()
+    assert np.abs(occm[:, d, d] - occd).max() < 1e-12
