@@ -59,3 +59,13 @@ def test_sigma_from_irreducible_q_equals_full_sum():
     assert np.abs(red_c - full_c).max() < 1e-12 * np.abs(full_c).max()
     assert np.abs(red_x - full_x).max() < 1e-12 * np.abs(full_x).max()
     assert len(c.ibz) == 4 and c.nq == 8
+
+
+def test_oh_stars_on_the_4x4x4_mesh():
+    """Oh on the 4 x 4 x 4 mesh: 10 irreducible q whose stars (sizes 1, 1, 3, 3, 6, 6, 8, 12, 12,
+    12, each dividing 48) tile all 64 q."""
+    c = sy.make_symmetric_crystal(n=4, nb=4, nocc=2, cut=1.2)
+    sizes = [len(c.reps[q]) for q in c.ibz]
+    assert len(c.ibz) == 10 and sum(sizes) == 64
+    assert all(48 % s == 0 for s in sizes)
+    assert sorted(sizes) == [1, 1, 3, 3, 6, 6, 8, 12, 12, 12]
