@@ -21,11 +21,17 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                        closed form and the residual of the linear system.
 * selfenergy        -- Eq. (sigc) and the product-basis form of Eq. (sigx);
                        pinned by brute-force Matsubara convolution on tiny
-                       inputs and the direct occupied-state sum.
+                       inputs (Nk = 1, and Nk = 3 with k - q != k and band
+                       energies that differ between k and k - q) and the
+                       direct occupied-state sum.
 * dyson_iw          -- diagonal Dyson (Eqs. dysongf-zcjk) posed in iω; pinned
                        by the zero and static self-energy closed forms.
 * pade / cpe / qp   -- analytic continuation (Sec. III.B.6); pinned by exact
-                       recovery of few-pole models and causality.
+                       recovery of few-pole models and causality. qp_solve finds
+                       every rising zero near eps on its own mesh centred on eps
+                       and refines it by Brent's method; pinned by the closed
+                       forms of one- and two-pole self-energies (several zeros,
+                       two zeros and a pole within 5 mHa) and the fallback.
 * mlp               -- not in the paper; pinned by central finite differences.
 * screen_tau        -- the paper's tau-domain form of Eq. (tildeW) on the uniform power
                        mesh (Sec. III.B.3); pinned by closed forms of one-mode and

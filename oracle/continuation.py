@@ -15,8 +15,6 @@ loops (test infrastructure; see the package docstring).
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 import scipy.optimize as _so
 
@@ -101,63 +99,68 @@ ETA = 1e-4  # real-axis offset (Ha) at which continued self-energies are evaluat
 
 
 def pade_resig(a, z):
-    return lambda E: pade_eval(a, z, np.array([E + 1j * ETA]))[0].real
+    """Re Sigma(E + i eta) of a Pade continued fraction, for a scalar or an array of E."""
+    return lambda E: pade_eval(a, z, np.asarray(E, float) + 1j * ETA).real
 
 
 def cpe_resig(b, x):
-    return lambda E: (cpe_kernel(x, np.array([E + 1j * ETA])) @ b)[0].real
+    """Re Sigma(E + i eta) of a CPE fit, for a scalar or an array of E."""
+    def f(E):
+        E = np.asarray(E, float)
+        return (cpe_kernel(x, E.reshape(-1) + 1j * ETA) @ b).real.reshape(E.shape)
+    return f
 
 
 # ---------------------------------------------------------------- QP
-QP_STEP = 0.005      # Ha: the scan visits the energies j * QP_STEP within eps +- QP_RANGE
-QP_RANGE = 1.0       # Ha
-QP_BISECT = 60
+QP_WINDOW = 1.0      # Ha: quasiparticle energies are searched within eps +- QP_WINDOW
+QP_H = 2.5e-4        # Ha: spacing of the sign search, on points eps + i QP_H
+
+
+def qp_roots(eps, sigx, vxc, resig):
+    """Every zero of F(E) = E - eps - sigx + vxc - Re Sigma^c(E) in eps +- QP_WINDOW at which F
+    rises (F' > 0, i.e. quasiparticle weight Z = 1/F' > 0), ascending.
+
+    Zeros are bracketed by the sign changes F(E_i) < 0 <= F(E_{i+1}) on the points
+    E_i = eps + i QP_H, |i| <= QP_WINDOW / QP_H (a mesh centred on the problem's own eps), and
+    each bracket is refined by Brent's method to the last bit."""
+    n = int(round(QP_WINDOW / QP_H))
+    Es = eps + QP_H * np.arange(-n, n + 1)
+    Fs = Es - eps - sigx + vxc - np.asarray(resig(Es), float)
+    F = lambda E: E - eps - sigx + vxc - float(np.asarray(resig(np.array([E])))[0])  # noqa: E731
+    roots = []
+    for i in np.nonzero((Fs[:-1] < 0.0) & (Fs[1:] >= 0.0))[0]:
+        if Fs[i + 1] == 0.0:
+            roots.append(float(Es[i + 1]))
+        else:
+            roots.append(_so.brentq(F, Es[i], Es[i + 1], xtol=1e-15, rtol=4 * np.finfo(float).eps, maxiter=200))
+    return roots
 
 
 def qp_solve(eps, sigx, vxc, resig, de=1e-6, tol=1e-12, maxit=100):
-    """Quasiparticle energy: root of F(E) = E - eps - sigx + vxc - Re Sigma^c(E) nearest eps
-    (G(w) = 1/[G0(w)^-1 - Sigma^xc(w) - Sigma^H] peaks where F vanishes).
-
-    F is scanned on the fixed energy grid E_j = j 0.005 Ha, for the integers j with
-    eps - 1 <= E_j <= eps + 1 Ha (j from ceil((eps - 1) / 0.005) to floor((eps + 1) / 0.005));
-    among the upward crossings F_j < 0 <= F_{j+1} (quasiparticle weight Z > 0) the one whose
-    midpoint is nearest eps is refined by 60 bisections. Without a crossing, Newton iteration from eps (central-difference
-    derivative, steps clamped to 0.5 Ha) is the fallback. Returns (E, Z, ok) with ok False for
-    the fallback or a Newton failure."""
-    F = lambda E: E - eps - sigx + vxc - resig(E)  # noqa: E731
-    j0 = math.ceil((eps - QP_RANGE) / QP_STEP)
-    j1 = math.floor((eps + QP_RANGE) / QP_STEP)
-    Es = [j * QP_STEP for j in range(j0, j1 + 1)]
-    Fs = [F(E) for E in Es]
-    best = None
-    for j in range(len(Es) - 1):
-        if Fs[j] < 0.0 <= Fs[j + 1]:
-            d = abs(0.5 * (Es[j] + Es[j + 1]) - eps)
-            if best is None or d < best[0]:
-                best = (d, j)
-    if best is not None:
-        lo, hi = Es[best[1]], Es[best[1] + 1]
-        for _ in range(QP_BISECT):
-            mid = 0.5 * (lo + hi)
-            if F(mid) < 0.0:
-                lo = mid
-            else:
-                hi = mid
-        E = 0.5 * (lo + hi)
+    """Quasiparticle energy (Sec. III.B.6): the pole of G(w) = 1/[w - eps - Sigma^x + Sigma_0 - Sigma^c(w)]
+    nearest the reference energy eps, i.e. the zero of F(E) = E - eps - sigx + vxc - Re Sigma^c(E)
+    with positive weight Z = 1/F'(E) that lies nearest eps (the paper takes one solution per
+    state; where F has several zeros this is the reading taken). The candidates are those of
+    qp_roots. Without any, Newton iteration from eps (central-difference derivative, steps
+    clamped to 0.5 Ha) is the fallback. Returns (E, Z, ok) with ok False for the fallback."""
+    roots = qp_roots(eps, sigx, vxc, resig)
+    r1 = lambda E: float(np.asarray(resig(np.array([E])))[0])  # noqa: E731
+    if roots:
+        E = min(roots, key=lambda r: abs(r - eps))
         ok = True
     else:
         E = float(eps)
         ok = False
         for _ in range(maxit):
-            Fv = F(E)
-            dF = 1.0 - (resig(E + de) - resig(E - de)) / (2 * de)
+            Fv = E - eps - sigx + vxc - r1(E)
+            dF = 1.0 - (r1(E + de) - r1(E - de)) / (2 * de)
             if dF == 0 or not np.isfinite(dF):
                 break
             step = max(-0.5, min(0.5, Fv / dF))
             E -= step
             if abs(step) < tol * max(1.0, abs(E)):
                 break
-    dS = (resig(E + de) - resig(E - de)) / (2 * de)
+    dS = (r1(E + de) - r1(E - de)) / (2 * de)
     return E, 1.0 / (1.0 - dS), ok
 
 

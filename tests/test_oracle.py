@@ -279,6 +279,58 @@ def test_sigma_brute_force_matsubara():
         assert np.abs(S[:, m_] - ref).max() < 5e-3 * np.abs(ref).max()
 
 
+def test_sigma_brute_force_matsubara_k_minus_q():
+    """Eq. (sigc) at Nk = 3 with q != 0, so that k - q != k and the bands at k - q differ from
+    those at k: Sigma^c_n(k|i w) of the chain against the direct Matsubara convolution
+    -1/(Omega N_k beta) sum_nu sum_j G_j(k - q|i w - i nu) a_jn^+ W~(i nu) a_jn, with G and the
+    Lindhard P written out here with the k - q index (k - q) mod Nk of the 3 x 1 x 1 mesh."""
+    beta, nk, nb, ni, iq, omega = 10.0, 3, 3, 2, 1, 1.7
+    cr = gi.make_crystal(13, nk, nb, 1, ni, beta, qlist=[iq])
+    # the generator pins the band edges; draw band energies that differ at every k instead
+    cr.eps = np.sort(np.random.default_rng(4).uniform(-1.0, 1.0, (nk, nb)), axis=1)
+    M = gi.m_for_q(cr, 0)                                         # [k, I, a, b], a at k - q
+    kmq = [(k - iq) % nk for k in range(nk)]
+    assert list(cr.kmq[0]) == kmq and all(kmq[k] != k for k in range(nk))
+    v = cr.v[0] * 0.05
+    g = gi.make_grid(beta, 48, 48, 48, ncont=4, lam=300.0)
+    G, occ = orc.green_tau0(cr.eps, g.tau, beta)
+    P = orc.polarization(M, G, cr.kmq[0], omega=omega)
+    W = orc.screen(orc.tau_to_nu(P, g), v)
+    Wt = orc.nu_to_tau(W, g)
+    sc, _, _ = orc.selfenergy(M, G, Wt, v, cr.kmq[0], occ, omega=omega)
+    S = orc.sigma_tau_to_iw(sc, g, cont=True)                    # [k, n, ncont]
+    # brute force over nu_n, |n| <= N
+    N = 20000
+    n = np.arange(-N, N + 1)
+    nu = 2 * np.pi * n / beta
+    f = 1.0 / (np.exp(beta * cr.eps) + 1.0)
+    L = np.zeros((len(n), ni, ni), complex)
+    for k in range(nk):
+        ka = kmq[k]
+        A = M[k].reshape(ni, nb * nb)
+        wgt = (f[ka][:, None] - f[k][None, :]).reshape(-1)                         # f_a(k-q) - f_b(k)
+        d = (cr.eps[k][None, :] - cr.eps[ka][:, None]).reshape(-1)
+        L += np.einsum("Ip,np,Jp->nIJ", A, wgt[None, :] / (1j * nu[:, None] - d[None, :]), A.conj())
+    L /= omega * nk
+    sv = np.sqrt(v)
+    Pi = sv[None, :, None] * L * sv[None, None, :]
+    Wnu = sv[None, :, None] * (np.linalg.inv(np.eye(ni)[None] - Pi) - np.eye(ni)[None]) * sv[None, None, :]
+    worst, slip = 0.0, 0.0
+    for k in range(nk):
+        A = M[k].reshape(ni, nb * nb)
+        dd = np.einsum("Ip,nIJ,Jp->np", A.conj(), Wnu, A).reshape(len(n), nb, nb)  # [nu, j, n]
+        for m_ in range(4):
+            wm = (2 * m_ + 1) * np.pi / beta
+            Gm = 1.0 / (1j * (wm - nu)[:, None] - cr.eps[kmq[k]][None, :])          # G_j(k-q|i w - i nu)
+            ref = -(Gm[:, :, None] * dd).sum((0, 1)) / (beta * omega * nk)
+            worst = max(worst, np.abs(S[k, :, m_] - ref).max() / np.abs(ref).max())
+            Gk = 1.0 / (1j * (wm - nu)[:, None] - cr.eps[k][None, :])               # the slip G_j(k)
+            bad = -(Gk[:, :, None] * dd).sum((0, 1)) / (beta * omega * nk)
+            slip = max(slip, np.abs(bad - ref).max() / np.abs(ref).max())
+    assert worst < 1e-4, worst             # measured 1.3e-5 (transform discretisation)
+    assert slip > 1e3 * 1e-4, slip         # the pin tells G at k - q from G at k (measured 2.1)
+
+
 # ----------------------------------------------------------------------- Dyson
 def test_dyson_zero_and_static(g1):
     cr = gi.make_crystal(3, 2, 4, 2, 2, g1.beta)
@@ -365,6 +417,53 @@ def test_qp_quadratic_closed_form():
     assert ok and abs(E - want) < 1e-12
     assert abs(Z - 1 / (1 + g2 / (want - E0) ** 2)) < 1e-6
     assert orc.band_gap(np.array([[-1, 0.5], [-0.8, 0.3]]), 1) == pytest.approx(1.1)
+
+
+def _two_pole_roots(a0, e, r):
+    """Real zeros of F(E) = E - a0 - sum_p r_p / (E - e_p) for two poles: the cubic
+    (E - a0)(E - e1)(E - e2) - r1 (E - e2) - r2 (E - e1) = 0 (all three real and rising for r > 0)."""
+    (e1, e2), (r1, r2) = e, r
+    c = np.polymul(np.polymul([1.0, -a0], [1.0, -e1]), [1.0, -e2])
+    c = np.polysub(c, np.polyadd(np.polymul([r1], [1.0, -e2]), np.polymul([r2], [1.0, -e1])))
+    z = np.roots(c)
+    assert np.abs(z.imag).max() < 1e-12
+    return np.sort(z.real)
+
+
+@pytest.mark.parametrize("case", ["separated", "close"])
+def test_qp_two_pole_closed_form(case):
+    """Several quasiparticle solutions (Sec. III.B.6 assumes one): with a two-pole Sigma^c every zero
+    of F rises (Z = 1 / (1 + sum_p r_p / (E - e_p)^2) > 0), and qp_solve must return the one nearest
+    eps, located independently of any energy mesh by the cubic's roots. The close case puts two zeros
+    and a pole within 5 mHa of eps."""
+    if case == "separated":
+        e, r, s = (-0.3, 0.4), (0.02, 0.03), 0.05
+        epss = np.linspace(-0.8, 0.8, 17)
+    else:
+        e, r, s = (-0.7, 0.2015), (0.01, 4e-6), -0.011
+        epss = [0.2017, 0.203, 0.20325]
+    for eps in epss:
+        sx, vxc = -1.0, -1.0 - s
+        def resig(E):
+            with np.errstate(divide="ignore"):      # a mesh point may sit on a pole: F = -inf there
+                return r[0] / (E - e[0]) + r[1] / (E - e[1])
+        zs = _two_pole_roots(eps + s, e, r)
+        want = zs[np.argmin(np.abs(zs - eps))]
+        E, Z, ok = orc.qp_solve(eps, sx, vxc, resig)
+        assert ok and abs(E - want) < 1e-12, (eps, E, zs)
+        assert abs(Z - 1.0 / (1.0 + r[0] / (want - e[0]) ** 2 + r[1] / (want - e[1]) ** 2)) < 1e-6
+        inwin = zs[np.abs(zs - eps) < orc.continuation.QP_WINDOW]
+        got = orc.continuation.qp_roots(eps, sx, vxc, resig)
+        assert len(got) == len(inwin) and np.abs(np.array(got) - inwin).max() < 1e-12
+    if case == "close":
+        assert np.sort(np.abs(zs - eps))[1] < 5e-3       # two zeros within 5 mHa of eps
+
+
+def test_qp_no_zero_in_window_falls_back():
+    """A static shift of 5 Ha puts the only zero outside eps +- 1 Ha: Newton from eps reaches it
+    (E = eps + 5) and the result is flagged."""
+    E, Z, ok = orc.qp_solve(0.3, -2.0, -2.0, lambda E: 5.0 + 0.0 * np.asarray(E))
+    assert not ok and abs(E - 5.3) < 1e-12 and abs(Z - 1.0) < 1e-6
 
 
 # ----------------------------------------------------------------------- learned CPE seed
