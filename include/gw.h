@@ -46,7 +46,7 @@ typedef enum {
 typedef enum {
   GW_FP64 = 0,    /* native FP64 (CUDA cores); the parity path */
   GW_FP16X2 = 1,  /* tcgen05 tensor cores: fp16 hi/lo split operands, 3 products, FP32 TMEM accumulation */
-  GW_BF16X3 = 2,  /* tcgen05 tensor cores: bf16 three-slice split, 6 products, FP32 TMEM accumulation */
+                  /* (value 2 is not used) */
   GW_F32X2 = 3,   /* float-float on the FP32 pipes: each value hi + lo in two FP32 (~44-bit significand) */
   GW_F32 = 4      /* plain FP32 on the CUDA cores (gw_screen only) */
 } gw_prec;
@@ -109,6 +109,12 @@ typedef struct {
 gw_status gw_create(gw_ctx** ctx, const gw_grid* grid, const gw_system* sys, int device,
                     void* stream);
 gw_status gw_destroy(gw_ctx* ctx);
+/* Waits for the context's stream and reports errors of its asynchronous work: GW_ECUDA for a
+ * CUDA error, GW_ETIMEOUT when a bounded device-side wait in a tensor-core contraction (the
+ * pipeline barriers of k_pol_tc / k_sig_tc, see GW_TUNE_WAIT_CYCLES) ran out since the last
+ * gw_sync: the kernel then stopped, let the copies and MMAs it had issued finish, freed its
+ * tensor memory and returned, and the outputs of those calls are undefined. The error word is
+ * cleared when it is reported, so the context stays usable. */
 gw_status gw_sync(gw_ctx* ctx);
 const char* gw_last_error(gw_ctx* ctx);
 
@@ -155,8 +161,9 @@ gw_status gw_tau_to_freq_many(gw_ctx* ctx, gw_stat stat, gw_dir dir, int count, 
 /* Screened interaction minus bare Coulomb, W~ = W - v (Sec. III.B.3), at the bosonic
  * sparse set, where Eq. (tildeW) is algebraic: Pi = v^1/2 P v^1/2, X = (1 - Pi)^-1 Pi,
  * W~ = v^1/2 X v^1/2, for the nqb q points iq0 .. iq0 + nqb - 1 at once. With ni a
- * multiple of 32 (ni <= 320) X = (1 - Pi)^-1 - 1 from a blocked in-place Gauss-Jordan
- * inversion; otherwise by elimination of [1 - Pi | Pi] (GW_FP64 only). No pivoting:
+ * multiple of 32 (every ni gw_create accepts; NI > 320 runs the pivot-row panels in
+ * passes) X = (1 - Pi)^-1 - 1 from a blocked in-place Gauss-Jordan inversion; the
+ * elimination of [1 - Pi | Pi] (GW_FP64 only, any ni) serves gw_screen_static. No pivoting:
  * 1 - Pi has Hermitian part >= 1.
  * prec: GW_FP64 (native FP64), GW_F32X2 (float-float arithmetic; relative error ~1e-12
  * per element) or GW_F32 (FP32 arithmetic, blocked inversion only; relative error of the
@@ -249,7 +256,7 @@ gw_status gw_screen_static(int nq, int nnu, int ni, const double* sqrt_v, const 
  *             Sigx_n(k) += -1/(Omega N_k) sum_j occ_j(k-q) sum_I v_I |M^I_jn|^2.
  * G_tau [nk][nb][ntau]; occ [nk][nb]; Wt_tau cplx [ntau][ni][ni] (Hermitian);
  * Sigc_tau [nk][nb][ntau] (real: W~(tau) Hermitian); Sigx [nk][nb] (may be NULL).
- * prec GW_FP64: both in FP64. GW_FP16X2 / GW_BF16X3: Sigc on the tensor cores, Sigx in
+ * prec GW_FP64: both in FP64. GW_FP16X2: Sigc on the tensor cores, Sigx in
  * float-float on the FP32 pipes (relative error ~1e-12). */
 gw_status gw_selfenergy(gw_ctx* ctx, int iq, const double* G_tau, const double* occ,
                         const double* Wt_tau, gw_prec prec, double* Sigc_tau, double* Sigx);
@@ -304,7 +311,11 @@ gw_status gw_mlp_loss_grad(gw_mlp* mlp, int64_t batch, const float* x, int nx, c
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr; loss as above. */
 gw_status gw_mlp_train_step(gw_mlp* mlp, int64_t batch, const float* x, int nx, const float* Acpe, float lr,
                             float* loss);
-/* Host copies of the FP32 parameters in parameter order (float [num_params]). */
+/* Waits for the network's stream; GW_ETIMEOUT when a bounded wait of its tensor-core GEMM ran out
+ * since the last sync (the results since then are undefined; the error is cleared). */
+gw_status gw_mlp_sync(gw_mlp* mlp);
+/* Host copies of the FP32 parameters in parameter order (float [num_params]); synchronises and
+ * reports like gw_mlp_sync. */
 gw_status gw_mlp_get_params(gw_mlp* mlp, float* params);
 gw_status gw_mlp_set_params(gw_mlp* mlp, const float* params);
 
@@ -346,13 +357,24 @@ gw_status gw_measure_alu(int device, double* fp64_tflops, double* fp32_tflops);
  * a branch of a multi-stream CUDA graph. NULL = the legacy default stream. */
 gw_status gw_set_stream(gw_ctx* ctx, void* stream);
 
-/* Schedule knobs of the tensor-core polarization, for the autotuner of the batched driver.
+/* Knobs of the tensor-core contractions.
  *  GW_TUNE_POL_SEG_CHUNKS: K chunks (32 pairs each) summed in one FP32 accumulator segment,
  *      1 .. 32 (default 32; fewer = more, smaller partials and a smaller accumulation error);
  *  GW_TUNE_POL_PART_MB: MiB of FP32 partial strips held at once (default 8192; the K segments
- *      run in passes beyond it), >= 1.
+ *      run in passes beyond it), >= 1;
+ *  GW_TUNE_WAIT_CYCLES: SM clock cycles a pipeline wait of k_pol_tc / k_sig_tc may take before it
+ *      gives up and the launch reports GW_ETIMEOUT at the next gw_sync, 1e3 .. 2^40 (default 4e9,
+ *      ~2 s at the GPU's top clock; a healthy wait takes microseconds);
+ *  GW_TUNE_FAULT_STALL: fault injection for tests of that detector, 0 or 1: with 1, the
+ *      MMA-issuing thread of every tensor-core contraction block first waits on a barrier that
+ *      nothing arrives on, so the wait runs out after the wait budget (the GPU stays usable).
  * Out-of-range values return GW_EINVAL. Results stay within the tensor-core error bound. */
-typedef enum { GW_TUNE_POL_SEG_CHUNKS = 0, GW_TUNE_POL_PART_MB = 1 } gw_tune;
+typedef enum {
+  GW_TUNE_POL_SEG_CHUNKS = 0,
+  GW_TUNE_POL_PART_MB = 1,
+  GW_TUNE_WAIT_CYCLES = 2,
+  GW_TUNE_FAULT_STALL = 3
+} gw_tune;
 gw_status gw_set_tuning(gw_ctx* ctx, gw_tune key, int64_t value);
 gw_status gw_kernel_time(gw_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
 

@@ -20,12 +20,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgw.so")
 
 GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ESINGULAR, GW_ENOCONV, GW_ETIMEOUT, GW_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-GW_FP64, GW_FP16X2, GW_BF16X3, GW_F32X2, GW_F32 = 0, 1, 2, 3, 4
+GW_FP64, GW_FP16X2, GW_F32X2, GW_F32 = 0, 1, 3, 4
 GW_BOSE, GW_FERMI = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU, GW_TAU_TO_IW_CONT = 0, 1, 2
 GW_PADE, GW_CPE = 0, 1
-GW_TUNE_POL_SEG_CHUNKS, GW_TUNE_POL_PART_MB = 0, 1
-PREC = {"fp64": GW_FP64, "fp16x2": GW_FP16X2, "bf16x3": GW_BF16X3}
+GW_TUNE_POL_SEG_CHUNKS, GW_TUNE_POL_PART_MB, GW_TUNE_WAIT_CYCLES, GW_TUNE_FAULT_STALL = 0, 1, 2, 3
+PREC = {"fp64": GW_FP64, "fp16x2": GW_FP16X2}
 
 _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW_ESINGULAR",
            -5: "GW_ENOCONV", -6: "GW_ETIMEOUT", -7: "GW_EUNSUPPORTED"}
@@ -36,7 +36,7 @@ EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau"
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
            "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning", "gw_measure_alu",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
-           "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_get_params", "gw_mlp_set_params",
+           "gw_mlp_forward", "gw_mlp_loss_grad", "gw_mlp_train_step", "gw_mlp_sync", "gw_mlp_get_params", "gw_mlp_set_params",
            "gw_cpe_features", "gw_cpe_fit_matrix", "gw_cpe_seed", "gw_cpe_iterations"]
 
 
@@ -136,7 +136,7 @@ def load_library(path=LIB_PATH):
         "gw_mlp_forward": [vp, i64, vp, vp],
         "gw_mlp_loss_grad": [vp, i64, vp, i32, vp, vp, vp],
         "gw_mlp_train_step": [vp, i64, vp, i32, vp, ctypes.c_float, vp],
-        "gw_mlp_get_params": [vp, vp], "gw_mlp_set_params": [vp, vp],
+        "gw_mlp_get_params": [vp, vp], "gw_mlp_set_params": [vp, vp], "gw_mlp_sync": [vp],
         "gw_cpe_features": [vp, i64, vp, i32, vp, vp],
         "gw_cpe_fit_matrix": [vp, i32, vp],
         "gw_cpe_seed": [vp, i64, vp, vp],
@@ -369,6 +369,9 @@ class MLP:
     def train_step(self, x, A, lr, loss=None):
         self._check(self.lib.gw_mlp_train_step(self.h, x.shape[0], _ptr(x), x.shape[1], _ptr(A), float(lr),
                                                _ptr(loss)), "gw_mlp_train_step")
+
+    def sync(self):
+        self._check(self.lib.gw_mlp_sync(self.h), "gw_mlp_sync")
 
     def get_params(self):
         p = np.zeros(self.num_params(), np.float32)

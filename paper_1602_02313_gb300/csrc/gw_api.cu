@@ -701,6 +701,11 @@ gw_status gw_create(gw_ctx** out, const gw_grid* g, const gw_system* s, int devi
     return GW_ENOMEM;
   }
   cudaMemcpy(c->d_widx, c->w_idx.data(), sizeof(int) * c->nw, cudaMemcpyHostToDevice);
+  if (cudaMalloc((void**)&c->d_err, 16) != cudaSuccess || cudaMemset(c->d_err, 0, 16) != cudaSuccess) {
+    cudaGetLastError();
+    gw_destroy(c);
+    return GW_ENOMEM;
+  }
 
   if (s->M) {
     c->d_M = s->M;
@@ -775,6 +780,7 @@ gw_status gw_destroy(gw_ctx* c) {
   if (c->d_cpe_seed) cudaFree(c->d_cpe_seed);
   if (c->d_widx) cudaFree(c->d_widx);
   if (c->d_tau) cudaFree(c->d_tau);
+  if (c->d_err) cudaFree(c->d_err);
   free_mixed(c);
   delete c;
   return GW_OK;
@@ -784,6 +790,16 @@ gw_status gw_sync(gw_ctx* c) {
   if (!c) return GW_EINVAL;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return set_err(c, GW_ECUDA, std::string("gw_sync: ") + cudaGetErrorString(e));
+  // a bounded wait in a tensor-core contraction that ran out since the last gw_sync
+  int h = 0;
+  if (cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_err(c, GW_ECUDA, "gw_sync: reading the device error word");
+  if (h != 0) {
+    cudaMemset(c->d_err, 0, sizeof(int));
+    return set_err(c, GW_ETIMEOUT,
+                   "gw_sync: a bounded device-side wait ran out in a tensor-core contraction (k_pol_tc / k_sig_tc); "
+                   "the outputs of the calls since the last gw_sync are undefined");
+  }
   return GW_OK;
 }
 
@@ -807,6 +823,14 @@ gw_status gw_set_tuning(gw_ctx* c, gw_tune key, int64_t value) {
     case GW_TUNE_POL_PART_MB:
       if (value < 1 || value > (1ll << 22)) return set_err(c, GW_EINVAL, "gw_set_tuning: partial MiB >= 1");
       c->pol_part_bytes = (size_t)value << 20;
+      return GW_OK;
+    case GW_TUNE_WAIT_CYCLES:
+      if (value < 1000 || value > (1ll << 40)) return set_err(c, GW_EINVAL, "gw_set_tuning: wait cycles in 1e3 .. 2^40");
+      c->wait_cycles = value;
+      return GW_OK;
+    case GW_TUNE_FAULT_STALL:
+      if (value != 0 && value != 1) return set_err(c, GW_EINVAL, "gw_set_tuning: stall injection is 0 or 1");
+      c->fault_stall = (int)value;
       return GW_OK;
   }
   return set_err(c, GW_EINVAL, "gw_set_tuning: unknown key");
@@ -846,7 +870,7 @@ gw_status gw_green_tau(gw_ctx* c, const double* eps, const double* sigx, const d
 gw_status gw_polarization(gw_ctx* c, int iq, const double* G, gw_prec prec, double* P) {
   if (!c || !G || !P || iq < 0 || iq >= c->nq) return GW_EINVAL;
   if (prec == GW_FP64) return launch_pol_fp64(c, iq, G, P);
-  if (prec == GW_FP16X2 || prec == GW_BF16X3) return launch_pol_mixed(c, iq, G, (int)prec, P);
+  if (prec == GW_FP16X2) return launch_pol_mixed(c, iq, G, (int)prec, P);
   return GW_EINVAL;
 }
 
@@ -886,7 +910,7 @@ gw_status gw_selfenergy(gw_ctx* c, int iq, const double* G, const double* occ, c
   gw_status st;
   if (prec == GW_FP64)
     st = launch_sigma_fp64(c, iq, G, W, S);
-  else if (prec == GW_FP16X2 || prec == GW_BF16X3)
+  else if (prec == GW_FP16X2)
     st = launch_sigma_mixed(c, iq, G, W, (int)prec, S);
   else
     return GW_EINVAL;

@@ -113,6 +113,9 @@ struct gw_ctx {
   size_t pade_bytes = 0;
   // tensor-core path
   gwi::MixedWork mw;
+  int* d_err = nullptr;                     // error word of the bounded device waits (read by gw_sync)
+  long long wait_cycles = 4000000000ll;     // clock cycles a tensor-core pipeline wait may take (~2 s)
+  int fault_stall = 0;                      // test fault injection: MMA issuers wait on a barrier nothing sets
   int pol_seg_chunks = 32;                  // K chunks per FP32 accumulation segment of P (<= 32)
   size_t pol_part_bytes = 8ull << 30;       // FP32 partial strips of P held at once
   // per-kernel timing (gw_kernel_timing): CUDA events recorded around selected launches

@@ -61,11 +61,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   unsigned char* sB = base + 16384;  // <= 256 x 128 B
   __shared__ uint64_t bar;
   __shared__ uint32_t tslot;
+  __shared__ int abort_g, no_dealloc;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 256;
   const int Nt = min(256, N - n0);
   if (tid == 0) {
     mbar_init(&bar, 1);
+    abort_g = 0;
+    no_dealloc = 0;
     fence_mbar_init();
   }
   if (warp == 0) tmem_alloc(&tslot, 256);
@@ -74,8 +77,8 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   tc_fence_after();
   const uint32_t tbase = tslot;
   const uint32_t id = idesc_f16(128, Nt, false, false);
-  bool ok = true;
-  for (int kc = 0; kc < K / 64; ++kc) {
+  int kc = 0;
+  for (; kc < K / 64; ++kc) {
     for (int e = tid; e < 128 * 8; e += GEMM_THREADS) {
       const int r = e >> 3, c = e & 7;
       const uint4 v = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + r) * K + kc * 64 + 8 * c);
@@ -96,10 +99,17 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
                 (kc > 0 || ks > 0) ? 1u : 0u);
       mma_commit(&bar);
     }
-    ok = ok && mbar_wait(&bar, kc & 1, err);
+    // a thread whose wait runs out stops the whole block after the barrier (abort_g is written
+    // only between the two barriers of an iteration, so every thread reads the same value)
+    if (!mbar_wait(&bar, kc & 1, err)) abort_g = 1;
     tc_fence_after();
     __syncthreads();
+    if (abort_g) break;
   }
+  // MMAs still running into TMEM complete before the block frees it; if they do not, it keeps it
+  if (abort_g && tid == 0 && !mbar_wait_drain(&bar, kc & 1)) no_dealloc = 1;
+  __syncthreads();
+  const bool ok = !abort_g;
   const int row = 32 * warp + lane;
   for (int c = 0; c < Nt; c += 16) {
     float v[16];
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, 256);
+  if (warp == 0 && !no_dealloc) tmem_dealloc(tbase, 256);
 }
 
 // ------------------------------------------------------------------ elementwise
@@ -510,10 +520,25 @@ gw_status gw_mlp_train_step(gw_mlp* m, int64_t batch, const float* x, int nx, co
   return refresh_half(m);
 }
 
+gw_status gw_mlp_sync(gw_mlp* m) {
+  if (!m) return GW_EINVAL;
+  if (cudaStreamSynchronize(m->stream) != cudaSuccess) return mlp_err(m, GW_ECUDA, "gw_mlp_sync: stream");
+  int h = 0;
+  if (cudaMemcpy(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mlp_err(m, GW_ECUDA, "gw_mlp_sync: reading the device error word");
+  if (h != 0) {
+    cudaMemset(m->err, 0, sizeof(int));
+    return mlp_err(m, GW_ETIMEOUT,
+                   "gw_mlp_sync: a bounded wait in the tensor-core GEMM ran out; results since the last sync are undefined");
+  }
+  return GW_OK;
+}
+
 gw_status gw_mlp_get_params(gw_mlp* m, float* params) {
   if (!m || !params) return GW_EINVAL;
   size_t off = 0;
-  cudaStreamSynchronize(m->stream);
+  gw_status st = gw_mlp_sync(m);
+  if (st != GW_OK) return st;
   for (int l = 0; l < m->nlayers; ++l) {
     const size_t nw = (size_t)m->dout[l] * m->din[l];
     cudaMemcpy(params + off, m->W[l], sizeof(float) * nw, cudaMemcpyDeviceToHost);

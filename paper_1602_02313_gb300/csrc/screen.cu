@@ -384,6 +384,8 @@ extern "C" gw_status gw_screen_static(int nq, int nnu, int ni, const double* sqr
     }
     scratch = g_scratch_ptr[dev];
   }
+  // an error left by the caller's own earlier work is reported, not cleared
+  if (cudaPeekAtLastError() != cudaSuccess) return GW_ECUDA;
   const int qpp = (int)(kScreenStaticBytes / per_q);  // q points per pass
   cudaStream_t st = (cudaStream_t)stream;
   for (int q0 = 0; q0 < nq; q0 += qpp) {

@@ -47,6 +47,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
   return false;
 }
 
+// Wait for work a block has already issued before it frees its resources; twice the budget of
+// mbar_wait, and false if even that runs out.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < 2 * kWaitBudget; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // Arrive on an mbarrier and add `bytes` to the transaction count it waits for.
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");

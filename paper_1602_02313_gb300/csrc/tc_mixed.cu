@@ -41,20 +41,31 @@ using namespace tc;
 
 constexpr float kScaleA = 256.0f;   // 2^8 on matrix elements (|M| < ~3)
 constexpr float kScaleW = 1.0f;     // W~ entries are O(v) <= 4 pi / 0.05
-constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+constexpr long long kDrainCycles = 4000000000ll;  // ~2 s at 2 GHz: waits for work already issued
 
-// Bounded mbarrier wait shared by all roles of a block: gives up after
-// kWaitCycles, or at once if another thread of the block has given up.
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+// Bounded mbarrier wait shared by all roles of a block: gives up after `budget` clock cycles
+// (the context's wait budget, ~2 s by default), or at once if another thread of the block has
+// given up; on giving up it raises the block's abort flag and records kErrTimeout in *err.
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       if (err) atomicExch(err, kErrTimeout);
       return false;
     }
   }
+  return true;
+}
+
+// Wait for work this block has already issued (bulk copies into its shared memory, MMAs into its
+// TMEM) before the block gives up its resources; ignores the abort flag, bounded by kDrainCycles.
+__device__ __forceinline__ bool drain_bar(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > kDrainCycles) return false;
   return true;
 }
 
@@ -82,9 +93,11 @@ constexpr int P_XT = 16384;                         // one X slice: 128 rows x 1
 constexpr int P_STAGE_BYTES = 2 * P_XT + 2 * 256 * 128;  // X hi, lo (128 rows) + Y hi, lo (<= 256 rows)
 
 struct PolSmem {
-  uint64_t full[2], empty[2], done;
+  uint64_t full[2], empty[2], done, never;  // never: nothing arrives on it (stall injection)
   uint32_t tslot;
-  int abort_flag;
+  int abort_flag;                           // any role gave up a wait
+  int abort_prod[2];                        // producer decision per chunk parity (uniform, see below)
+  int no_dealloc;                           // issued work did not drain: keep TMEM, report only
 };
 
 __device__ __forceinline__ size_t ys_tile(int k, int c, int iblk, int sl, int cpk, int nib) {
@@ -137,7 +150,7 @@ __global__ void k_split_y(const double2* __restrict__ Mq, int nk, int ni, int np
 __global__ void __launch_bounds__(PT_THREADS, 1)
     k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
              int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, float* __restrict__ part,
-             int* __restrict__ err) {
+             int* __restrict__ err, long long wait_cycles, int stall) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
@@ -159,7 +172,10 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       mbar_init(&S.empty[s], 1);
     }
     mbar_init(&S.done, 1);
+    mbar_init(&S.never, 1);
     S.abort_flag = 0;
+    S.abort_prod[0] = S.abort_prod[1] = 0;
+    S.no_dealloc = 0;
     fence_mbar_init();
   }
   if (warp == 8) tmem_alloc(&S.tslot, 512);
@@ -202,14 +218,22 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       }
     };
     Item cur[2], nxt[2];
+    int last0 = -1, last1 = -1;  // (thread 0) last chunk whose copies went to stage 0 / 1
     if (nchunk > 0) fetch(0, cur);
     for (int i = 0; i < nchunk; ++i) {
       const int s = i & 1;
-      if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
+      // All 256 producer threads take the same go / stop decision for chunk i (their flag slot is
+      // written only before this barrier, and slot i & 1 is not written again before every thread
+      // has read it), so every chunk whose copies are issued gets all its arrivals and its full
+      // barrier completes once the bytes land: the drain below can wait for it.
+      if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err, wait_cycles)) S.abort_prod[s] = 1;
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (S.abort_prod[s]) break;
       unsigned char* st = base + s * P_STAGE_BYTES;
       if (tid == 0) {
         // Y: rows [c0, c0 + N) = whole or leading parts of 128-row blocks, hi and lo slices
         const int g = g0 + i, k = g / cpk, c = g % cpk;
+        if (s) last1 = i; else last0 = i;
         mbar_arrive_expect_tx(&S.full[s], 2 * ybytes_slice);
         for (int r0 = 0; r0 < N; r0 += 128) {
           const int rows = min(128, N - r0);
@@ -238,17 +262,22 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       }
       fence_proxy_async_smem();
       mbar_arrive(&S.full[s]);
-      if (S.abort_flag) break;
 #pragma unroll
       for (int j = 0; j < 2; ++j) cur[j] = nxt[j];
+    }
+    // bulk copies still in flight into this block's shared memory land before it exits
+    if (tid == 0) {
+      if (last0 >= 0 && !drain_bar(&S.full[0], (last0 >> 1) & 1)) S.no_dealloc = 1;
+      if (last1 >= 0 && !drain_bar(&S.full[1], (last1 >> 1) & 1)) S.no_dealloc = 1;
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t id = idesc_f16(128, N, false, false), idn = idesc_f16(128, N, false, true);
     const uint32_t dre = tbase, dim = tbase + N;
+    if (stall) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall: runs out
     for (int i = 0; i < nchunk; ++i) {
       const int s = i & 1;
-      if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) break;
+      if (S.abort_flag || !wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err, wait_cycles)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(base + s * P_STAGE_BYTES);
       const uint32_t xh = st, xl = st + P_XT, yh = st + 2 * P_XT, yl = yh + ybytes_slice;
@@ -269,11 +298,12 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       mma_commit(&S.empty[s]);
     }
     mma_commit(&S.done);
+    if (!drain_bar(&S.done, 0)) S.no_dealloc = 1;  // every MMA issued here has completed
   }
 
   // ------------------------------------------------------------ epilogue: FP32 partial strips (8 warps)
   if (warp < 8) {
-    const bool ok = nchunk > 0 && wait_bar(&S.done, 0, &S.abort_flag, err);
+    const bool ok = nchunk > 0 && wait_bar(&S.done, 0, &S.abort_flag, err, wait_cycles) && !S.abort_flag;
     tc_fence_after();
     const int quad = warp & 3, half = warp >> 2;
     const int row = 32 * quad + lane;
@@ -298,7 +328,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 8) tmem_dealloc(tbase, 512);
+  if (warp == 8 && !S.no_dealloc) tmem_dealloc(tbase, 512);
 }
 
 // h + l += x with the rounding error of h + x kept exactly in l (Knuth's two-sum)
@@ -462,8 +492,10 @@ constexpr int S_ATILE = 128 * 64;                   // 128 rows x 64 B (32 fp16)
 
 struct SigSmem {
   uint64_t full[2], empty[2], col[32], tempty;  // col[c]: K chunk c of the current unit is done
+  uint64_t fin, never;                          // fin: all MMAs done; never: stall injection
   uint32_t tslot;
   int abort_flag;
+  int no_dealloc;
   float red[4][128];
 };
 
@@ -476,7 +508,8 @@ struct SigSmem {
 // epilogue sums d_p over the parts of a tau before writing it.
 __global__ void __launch_bounds__(ST_THREADS, 1)
     k_sig_tc(const __half* __restrict__ XS, const float2* __restrict__ XE, const __half* __restrict__ WS, int ni,
-             int nh, int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err) {
+             int nh, int npb, int ntau, double* __restrict__ D, int np, int* __restrict__ err, long long wait_cycles,
+             int stall) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
   const int NC = ni / nh;  // output columns per part
@@ -497,7 +530,10 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
     }
     for (int c = 0; c < 32; ++c) mbar_init(&S.col[c], 1);
     mbar_init(&S.tempty, ST_EPI_WARPS * 32);
+    mbar_init(&S.fin, 1);
+    mbar_init(&S.never, 1);
     S.abort_flag = 0;
+    S.no_dealloc = 0;
     fence_mbar_init();
   }
   if (warp == MW) tmem_alloc(&S.tslot, 512);
@@ -510,12 +546,14 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
     // ------------------------------------------------------------ producer: bulk copies per chunk
     if (lane == 0) {
       int i = 0;  // running chunk index (stage i & 1)
+      int last0 = -1, last1 = -1;  // last chunk whose copies went to stage 0 / 1
       for (int u = 0; u < nunit && !S.abort_flag; ++u) {
         const int it = u / nh, h = u % nh;
         const int kend = min(nkc, ((h + 1) * NC) >> 5);
         for (int kc = 0; kc < kend; ++kc, ++i) {
           const int s = i & 1;
-          if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err)) break;
+          if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err, wait_cycles)) break;
+          if (s) last1 = i; else last0 = i;
           const int j0 = max(h * NC, 32 * kc);      // first output column reached
           const int rows = (h + 1) * NC - j0;       // B rows (output columns) copied
           const int roff = j0 - h * NC;             // their offset inside the part
@@ -527,19 +565,24 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
             bulk_g2s(st + a_bytes + sl * BT + roff * 64, w0 + (size_t)sl * ni * 32, (uint32_t)rows * 64, &S.full[s]);
         }
       }
+      // the copies of every issued chunk land before the block exits (one arrival per chunk,
+      // so its full barrier completes once its bytes are in)
+      if (last0 >= 0 && !drain_bar(&S.full[0], (last0 >> 1) & 1)) S.no_dealloc = 1;
+      if (last1 >= 0 && !drain_bar(&S.full[1], (last1 >> 1) & 1)) S.no_dealloc = 1;
     }
   } else if (warp == MW) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int i = 0;
       bool live = true;
-      for (int u = 0; u < nunit && live; ++u) {
+      if (stall) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall: runs out
+      for (int u = 0; u < nunit && live && !S.abort_flag; ++u) {
         const int h = u % nh;
         const int kend = min(nkc, ((h + 1) * NC) >> 5);
-        if (u > 0 && !wait_bar(&S.tempty, (u - 1) & 1, &S.abort_flag, err)) break;
+        if (u > 0 && !wait_bar(&S.tempty, (u - 1) & 1, &S.abort_flag, err, wait_cycles)) break;
         for (int kc = 0; kc < kend; ++kc, ++i) {
           const int s = i & 1;
-          if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err)) {
+          if (!wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err, wait_cycles)) {
             live = false;
             break;
           }
@@ -576,6 +619,8 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
           mma_commit(&S.col[kc]);
         }
       }
+      mma_commit(&S.fin);
+      if (!drain_bar(&S.fin, 0)) S.no_dealloc = 1;  // every MMA issued here has completed
     }
   } else {
     // ------------------------------------------------------------ epilogue: d_p(tau), 16 warps
@@ -606,7 +651,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
           }
           // the K chunk c that finishes this block's columns runs in parts h' >= h of every tau
           // (32 c < (h' + 1) NC), so before this unit it has completed tau (nh - h) times
-          ok = wait_bar(&S.col[(h * NC + n0) >> 5], (it * (nh - h)) & 1, &S.abort_flag, err);
+          ok = wait_bar(&S.col[(h * NC + n0) >> 5], (it * (nh - h)) & 1, &S.abort_flag, err, wait_cycles);
           tc_fence_after();
           if (!ok) break;
           float v1[16], v2[16];
@@ -640,7 +685,7 @@ __global__ void __launch_bounds__(ST_THREADS, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == MW) tmem_dealloc(tbase, 512);
+  if (warp == MW && !S.no_dealloc) tmem_dealloc(tbase, 512);
 }
 
 // Sigc_n(k|tau) += pref sum_a G_a(k-q|tau) d_(a,n)(tau); deterministic (no atomics).
@@ -722,14 +767,12 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   if (c->mw.dacc != meta_before) c->mw.strips_ready = false;
   int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
   int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
-  int* d_err = d_strip_of + strip_of.size();
   if (!c->mw.strips_ready) {  // depends on ni only: uploaded on the first call
     if (cudaMemcpy(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice) != cudaSuccess)
       return set_err(c, GW_ECUDA, "P strips upload");
     c->mw.strips_ready = true;
   }
-  cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   if (ni % 128) cudaMemsetAsync(d_ys, 0, ys_bytes, c->stream);  // rows >= ni of the last block stay zero
   const double2* Mq = (const double2*)m_block(c, iq);
   if (!Mq) return GW_ECUDA;
@@ -747,7 +790,8 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
     const int ns = std::min(seg_pass, nseg - s0);
     kt_begin(c, "k_pol_tc");
     k_pol_tc<<<base_units * ns, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips,
-                                                               d_strips, nseg, s0, d_part, d_err);
+                                                               d_strips, nseg, s0, d_part, c->d_err, c->wait_cycles,
+                                                               c->fault_stall);
     kt_end(c);
     if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
     k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
@@ -776,8 +820,6 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   __half* WS = XS + xbytes / sizeof(__half);
   double* D = (double*)((char*)c->mw.mslices + xbytes + wbytes);
   float2* XE = (float2*)((char*)D + dbytes);
-  int* d_err = (int*)((char*)XE + ebytes);
-  cudaMemsetAsync(d_err, 0, sizeof(int), c->stream);
   if (c->mw.iq != iq || c->mw.prec != prec) {
     const double2* Mq = (const double2*)m_block(c, iq);
     if (!Mq) return GW_ECUDA;
@@ -795,7 +837,8 @@ gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W
   cudaFuncSetAttribute(k_sig_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid(npb, c->nk);
   kt_begin(c, "k_sig_tc");
-  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, nh, npb, c->ntau, D, np, d_err);
+  k_sig_tc<<<grid, ST_THREADS, smem, c->stream>>>(XS, XE, WS, c->ni, nh, npb, c->ntau, D, np, c->d_err,
+                                                  c->wait_cycles, c->fault_stall);
   kt_end(c);
   if ((st = check_launch(c, "sig_tc")) != GW_OK) return st;
   const int64_t n = (int64_t)c->nk * c->nb * c->ntau;

@@ -55,6 +55,10 @@ def test_screen_static_matches_screen():
         got = W.cpu().numpy()
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err < TOL, f"call {call}: rel err {err:.3e}"
+    # and directly against the oracle's solve of Eq. (tildeW) in i nu, one q point
+    import oracle as orc
+    err = np.abs(got[1] - orc.screen(P[1], cr.v[1])).max() / np.abs(ref[1]).max()
+    assert err < TOL, f"vs oracle: rel err {err:.3e}"
     # sizes beyond the built-in scratch are rejected
     assert lib.gw_screen_static(1, 200, 256, ctypes.c_void_p(sv.data_ptr()), ctypes.c_void_p(Pd.data_ptr()),
                                 ctypes.c_void_p(W.data_ptr()), ctypes.c_void_p(info.data_ptr()), stream) == gw.GW_EINVAL
