@@ -46,6 +46,9 @@ Parity status per function (what pins it; see tests/test_oracle_*.py):
                        Hermiticity and covariance under a unitary change of bands. Its matrix
                        Dyson update (dyson_matrix_iw) is pinned by the downfolding closed form
                        of a pole self-energy, its diagonal reduction and unitary covariance.
+* symmetry          -- the star sum of Sec. III.C (the self-energy of an irreducible q carried
+                       to every member of its star); pinned by the equality of the reduced sum
+                       and the full sum over the q mesh on a synthetic Oh crystal.
 """
 from .gw import *  # noqa: F401,F403
 from .transforms import transform_matrices  # noqa: F401
@@ -53,5 +56,6 @@ from . import mlp  # noqa: F401
 from . import screen_tau  # noqa: F401
 from . import dyson_tau  # noqa: F401
 from . import offdiag  # noqa: F401
+from . import symmetry  # noqa: F401
 from .continuation import (pade_coeffs, pade_eval, cpe_grid, cpe_kernel, cpe_fit,  # noqa: F401
                            cpe_eval, qp_solve, band_gap, pade_resig, cpe_resig, ETA)

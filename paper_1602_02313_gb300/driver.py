@@ -45,11 +45,11 @@ class Chain:
         self.nk, self.nb, self.ni, self.ntau = cr.nk, cr.nb, cr.ni, len(g.tau)
         self.nnu, self.nw, self.ncont = len(g.nu_idx), len(g.w_idx), g.ncont
         self.prec = prec
-        # the dielectric solve: native FP64 on the FP64 chain, FP32 on the mixed one (its input P
-        # carries the ~1e-6 error of the fp16-split contraction; screen_prec=GW_F32X2 selects
-        # float-float). The bosonic transforms: FP64 on the FP64 chain, float-float on the mixed one.
+        # the dielectric solve: native FP64 on the FP64 chain, float-float (FP64-grade, ~44-bit
+        # significand) on the mixed one; screen_prec=GW_F32 selects plain FP32. The bosonic
+        # transforms: FP64 on the FP64 chain, float-float on the mixed one.
         if screen_prec is None:
-            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32
+            screen_prec = GW_FP64 if prec == GW_FP64 or ctx.cr.ni % 32 else GW_F32X2
         self.screen_prec = screen_prec
         # crystal symmetry (Sec. III.C): iqs are the irreducible q points and star[j] the
         # device int32 [nrep][nk] map k -> R^-1 k of each member of iqs[j]'s star; every q's

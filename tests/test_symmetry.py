@@ -53,9 +53,8 @@ def test_sigma_from_irreducible_q_equals_full_sum():
     full_x = sum(contrib[q][1] for q in range(c.nq))
     red_c, red_x = np.zeros_like(full_c), np.zeros_like(full_x)
     for q in c.ibz:
-        for inv in kinv_maps(c, q):
-            red_c += contrib[q][0][inv]
-            red_x += contrib[q][1][inv]
+        red_c += orc.symmetry.sigma_star(contrib[q][0], kinv_maps(c, q))
+        red_x += orc.symmetry.sigma_star(contrib[q][1], kinv_maps(c, q))
     assert np.abs(red_c - full_c).max() < 1e-12 * np.abs(full_c).max()
     assert np.abs(red_x - full_x).max() < 1e-12 * np.abs(full_x).max()
     assert len(c.ibz) == 4 and c.nq == 8
