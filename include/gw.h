@@ -225,10 +225,30 @@ gw_status gw_sigma_star(gw_ctx* ctx, int nrep, const int* kinv, int64_t ncol, co
  *   Sigma^c_nm(k|tau) += -1/(Omega N_k) sum_j G_j(k-q|tau) sum_IJ conj(M^I_jn) W~_IJ(tau) M^J_jm,
  *   Sigma^x_nm(k)     += -1/(Omega N_k) sum_j occ_j(k-q) sum_I v_I conj(M^I_jn) M^I_jm.
  * G_tau [nk][nb][ntau], occ [nk][nb] (may be NULL when Sx is), Wt_tau cplx [ntau][ni][ni];
- * S_tau cplx [nk][nb][nb][ntau]; Sx cplx [nk][nb][nb] (may be NULL). FP64 on the CUDA cores;
- * GW_EINVAL when (ni nb + nb^2) 16 bytes exceed 200 KiB (one (k, tau)'s working set). */
+ * S_tau cplx [nk][nb][nb][ntau]; Sx cplx [nk][nb][nb] (may be NULL). FP64 on the CUDA cores,
+ * W~ a_j formed in chunks of rows so any ni fits; GW_EINVAL when the nb x nb accumulator of one
+ * (k, tau) and 8 rows of W~ a_j do not fit in 200 KiB of shared memory (nb > 109). */
 gw_status gw_selfenergy_offdiag(gw_ctx* ctx, int iq, const double* G_tau, const double* occ, const double* Wt_tau,
                                 double* S_tau, double* Sx);
+
+/* Dyson update of the full band matrix of G (Eq. dysonGF of Sec. II without the diagonal
+ * approximation of Sec. III.B, whose off-diagonal form the paper leaves for later work), the
+ * consumer of gw_selfenergy_offdiag. Posed at the sparse fermionic set like gw_green_tau:
+ *   G(k|i w) = [i w - H~ - Sigma^c(k|i w)]^-1,   H~ = diag(eps) + Sx - vxc,
+ * Sigma^c(i w) from Sc_tau by the fermionic forward transform (Eq. trans, complex-linear); the
+ * tail (i w - H~)^-1 is subtracted and added back exactly in tau as U diag(G0(lambda, tau)) U^+
+ * with H~ = U diag(lambda) U^+ (cyclic Jacobi on the device, Hermitian part of H~); the
+ * remainder goes back to tau through the fermionic backward map of the real tau-functions
+ * Re G_nm and Im G_nm.
+ * eps [nk][nb]; Sx, vxc cplx [nk][nb][nb] (Hermitian; either may be NULL for zero);
+ * Sc_tau cplx [nk][nb][nb][ntau] (NULL for zero); G_tau out cplx [nk][nb][nb][ntau];
+ * occ out cplx [nk][nb][nb] = -G(beta^-); info out (device) int [nk]: 0, 1 when the eigensolver
+ * did not reach 1e-15 relative off-diagonal norm in 40 sweeps (G is still written), or 2 + j
+ * for a zero pivot at elimination step j of some frequency (that k's G and occ not written).
+ * FP64 on the CUDA cores; nb <= 256 (else GW_EINVAL); workspace
+ * ~ nk nb^2 (4 nw + 2) 16 bytes, grown on use. */
+gw_status gw_dyson_matrix(gw_ctx* ctx, const double* eps, const double* Sx, const double* vxc, const double* Sc_tau,
+                          double* G_tau, double* occ, int* info);
 
 /* Allocation-free variant of gw_screen. The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory at the time of the call, such as

@@ -32,7 +32,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
 
 # Every symbol declared in include/gw.h.
 EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
-           "gw_tau_to_freq", "gw_tau_to_freq_many", "gw_screen", "gw_screen_tau", "gw_dyson_tau", "gw_sigma_star", "gw_selfenergy_offdiag", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
+           "gw_tau_to_freq", "gw_tau_to_freq_many", "gw_screen", "gw_screen_tau", "gw_dyson_tau", "gw_sigma_star", "gw_selfenergy_offdiag", "gw_dyson_matrix", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
            "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning", "gw_measure_alu",
            "gw_screen_static", "gw_mlp_create", "gw_mlp_destroy", "gw_mlp_last_error", "gw_mlp_num_params",
@@ -117,6 +117,7 @@ def load_library(path=LIB_PATH):
         "gw_dyson_tau": [vp, i64, i32, vp, vp, vp, vp, vp, vp],
         "gw_sigma_star": [vp, i32, vp, i64, vp, vp],
         "gw_selfenergy_offdiag": [vp, i32, vp, vp, vp, vp, vp],
+        "gw_dyson_matrix": [vp, vp, vp, vp, vp, vp, vp, vp],
         "gw_screen": [vp, i32, i32, vp, i32, vp, vp],
         "gw_selfenergy": [vp, i32, vp, vp, vp, i32, vp, vp],
         "gw_continue": [vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp, vp],
@@ -284,6 +285,13 @@ class GW:
         """S: complex128 [nk][nb][nb][ntau], Sx: complex128 [nk][nb][nb] or None (both accumulated)."""
         self._check(self.lib.gw_selfenergy_offdiag(self.h, int(iq), _ptr(G), _ptr(occ), _ptr(W), _ptr(S), _ptr(Sx)),
                     "gw_selfenergy_offdiag")
+
+    def dyson_matrix(self, eps, Sx, vxc, Sc_tau, G, occ, info):
+        """Full-matrix Dyson update: eps [nk][nb]; Sx, vxc complex128 [nk][nb][nb] or None; Sc_tau
+        complex128 [nk][nb][nb][ntau] or None; G complex128 [nk][nb][nb][ntau], occ complex128
+        [nk][nb][nb], info int32 [nk] (outputs)."""
+        self._check(self.lib.gw_dyson_matrix(self.h, _ptr(eps), _ptr(Sx), _ptr(vxc), _ptr(Sc_tau), _ptr(G), _ptr(occ),
+                                             _ptr(info)), "gw_dyson_matrix")
 
     def screen(self, iq0, nqb, P_iv, W_iv, info, prec=GW_FP64):
         self._check(self.lib.gw_screen(self.h, iq0, nqb, _ptr(P_iv), int(prec), _ptr(W_iv), _ptr(info)), "gw_screen")

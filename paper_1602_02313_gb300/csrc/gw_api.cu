@@ -769,6 +769,7 @@ gw_status gw_destroy(gw_ctx* c) {
   if (c->ff_ws) cudaFree(c->ff_ws);
   if (c->d_tsys) cudaFree(c->d_tsys);
   if (c->d_dyt) cudaFree(c->d_dyt);
+  if (c->d_dm) cudaFree(c->d_dm);
   c->ff_ws = nullptr;
   double* bufs[] = {c->d_sqrtv, c->d_v,       c->d_M_own, c->d_Bfwd,  c->d_Ffwd,  c->d_Fcont, c->d_Bbwd,
                     c->d_Fbwd,  c->d_Fbwd_beta, c->d_aug,   c->d_cpe_x, c->d_cpe_A, c->d_cpe_N, c->d_cpe_tab, c->d_cpe_b,

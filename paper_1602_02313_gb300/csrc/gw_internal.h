@@ -98,6 +98,8 @@ struct gw_ctx {
   void* ff_ws = nullptr;        // float-float copies of a bosonic transform's input
   void* d_tsys = nullptr;       // gw_screen_tau: two copies of the augmented system + increments
   size_t tsys_bytes = 0;
+  void* d_dm = nullptr;         // gw_dyson_matrix: Sigma^c(i w), eigenpairs, augmented systems, remainders
+  size_t dm_bytes = 0;
   void* d_dyt = nullptr;        // gw_dyson_tau: augmented systems of a chunk of states + the mesh
   size_t dyt_bytes = 0;
   size_t ff_ws_bytes = 0;  // real [1201][ngrid]: Re Phi_m on the QP scan grid

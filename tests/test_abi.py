@@ -82,3 +82,5 @@ def test_invalid_arguments_rejected_on_host(gw):
     assert lib.gw_dyson_tau(None, 1, 4, None, None, None, None, None, None) == gw.GW_EINVAL
     assert lib.gw_sigma_star(None, 1, None, 1, None, None) == gw.GW_EINVAL
     assert lib.gw_selfenergy_offdiag(None, 0, None, None, None, None, None) == gw.GW_EINVAL
+    assert lib.gw_dyson_matrix(None, None, None, None, None, None, None, None) == gw.GW_EINVAL
+    assert lib.gw_mlp_sync(None) == gw.GW_EINVAL

@@ -54,3 +54,26 @@ def test_offdiag_selfenergy_vs_oracle(gw):
     print(f"off-diagonal Sigma: GPU vs oracle {e:.1e} (Sigma^x {ex:.1e}); diagonal vs gw_selfenergy {ed:.1e}")
     assert e < 1e-10 and ex < 1e-10 and ed < 1e-12
     ctx.close()
+
+
+def test_offdiag_selfenergy_chunked_rows(gw):
+    """Nb = 64 and NI = 256 (the nk64_nb64 band and basis sizes): W~ a_j no longer fits beside the
+    accumulator, so it is formed in chunks of rows (136 + a ragged 120); against the oracle."""
+    import torch
+    cr = gi.make_crystal(44, 2, 64, 32, 256, 60.0, qlist=[1])
+    gr = gi.make_grid(60.0, 8, 8, 8, ncont=16)
+    ctx = gw.GW(gr, cr, omega=1.3)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    rng = np.random.default_rng(45)
+    X = rng.standard_normal((gr.ntau, cr.ni, 16)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 16))
+    W = -(X @ np.conj(np.swapaxes(X, 1, 2))) / 16
+    c16 = dict(dtype=torch.complex128, device="cuda")
+    S = torch.zeros((cr.nk, cr.nb, cr.nb, gr.ntau), **c16)
+    Sx = torch.zeros((cr.nk, cr.nb, cr.nb), **c16)
+    ctx.selfenergy_offdiag(0, dev(G), dev(occ), dev(W), S, Sx)
+    ctx.sync()
+    sc, sx = od.selfenergy_offdiag(gi.m_for_q(cr, 0), G, W, cr.v[0], cr.kmq[0], occ, omega=1.3)
+    e, ex = rel(S.cpu().numpy(), sc), rel(Sx.cpu().numpy(), sx)
+    print(f"off-diagonal Sigma, NI 256 in row chunks: {e:.1e} (Sigma^x {ex:.1e})")
+    assert e < 1e-10 and ex < 1e-10
+    ctx.close()
