@@ -19,8 +19,10 @@ Sec. "Computational Details"):
 * plane-wave matrix elements M^I_ab(k, q) (paper Eq. mmatrix) replaced by
   complex Gaussian numbers with E|M|^2 = 1/Nb, drawn from Philox4x32-10
   (Salmon, Moraes, Dror, Shaw, SC'11) keyed by the seed, with the flat index
-  of (q, k, I, a, b) as counter, then Box-Muller. The GPU library implements
-  the same published generator on its own; integer streams are bitwise equal.
+  of (q, k, I, a, b) as counter, then Box-Muller in FP32 with the logarithm,
+  sine and cosine evaluated by a fixed sequence of round-to-nearest FP32
+  operations (series written out here). The GPU library implements the same
+  generator on its own; the matrix elements are bitwise equal.
 
 Grid (discretisation input, passed explicitly to both sides):
 
@@ -83,19 +85,70 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
     return c0, c1, c2, c3
 
 
-def _u53_open0(hi, lo):
-    """53-bit uniform on (0, 1] from two 32-bit words: (m + 1) * 2^-53."""
-    m = (hi << np.uint64(21)) | (lo >> np.uint64(11))
-    return (m.astype(np.float64) + 1.0) * 2.0 ** -53
+# ---------------------------------------------------------------------------
+# Box-Muller in FP32 with a fixed sequence of round-to-nearest operations.
+# The logarithm and the sine / cosine are not library calls but the evaluations below: only
+# IEEE-754 round-to-nearest FP32 additions, multiplications, one division and one square root,
+# in a fixed order, so that the GPU generator (which performs the same operations with
+# explicitly rounded intrinsics) produces bit-identical matrix elements.
+#   ln u: u = 2^e m with m in [sqrt(1/2), sqrt(2)) (exact), ln m = 2 atanh(s), s = (m - 1)/(m + 1),
+#         by the odd series 2 (s + s^3/3 + ... + s^11/11) (|s| <= 0.172, truncation < 2e-9);
+#         ln u = e ln 2 + ln m.
+#   cos / sin (2 pi u): t = 4 u splits exactly into the quadrant o and f in [0, 1); x = (pi/2) f;
+#         Taylor series of sin x to x^13 and of cos x to x^12 (truncation < 1e-8 on [0, pi/2]);
+#         the quadrant by exact sign and order changes.
+# The series coefficients are 1/k and 1/k! rounded to FP32.
+# ---------------------------------------------------------------------------
+_F = np.float32
+_LN2 = _F(0.6931471805599453)
+_HALF_PI = _F(1.5707963267948966)
+_SQRT_HALF = _F(0.7071067811865476)
+_ATANH_C = [_F(1.0 / k) for k in (11, 9, 7, 5, 3)]                       # s^11 .. s^3 terms
+_SIN_C = [_F((-1.0) ** (k // 2) / math.factorial(k)) for k in (13, 11, 9, 7, 5, 3)]
+_COS_C = [_F((-1.0) ** (k // 2) / math.factorial(k)) for k in (12, 10, 8, 6, 4, 2)]
 
 
-def _u53(hi, lo):
-    """53-bit uniform on [0, 1) from two 32-bit words: m * 2^-53."""
-    m = (hi << np.uint64(21)) | (lo >> np.uint64(11))
-    return m.astype(np.float64) * 2.0 ** -53
+def log_f32(u):
+    """ln u for float32 u in (0, 1], by the fixed evaluation described above."""
+    u = np.asarray(u, np.float32)
+    m, e = np.frexp(u)                        # u = m 2^e, m in [0.5, 1)
+    low = m < _SQRT_HALF
+    m = np.where(low, m * _F(2.0), m)
+    e = np.where(low, e - 1, e).astype(np.float32)
+    f = m - _F(1.0)                           # exact (Sterbenz)
+    s = f / (_F(2.0) + f)
+    z = s * s
+    p = z * _ATANH_C[0] + _ATANH_C[1]
+    for c in _ATANH_C[2:]:
+        p = p * z + c
+    p = p * z                                 # s^2 / 3 + s^4 / 5 + ...
+    s2 = s + s
+    lm = s2 + s2 * p
+    return e * _LN2 + lm
 
 
-TWO_PI = 6.283185307179586  # fp64(2 pi); the GPU generator uses the same literal
+def sincos_turn_f32(u):
+    """(cos 2 pi u, sin 2 pi u) for float32 u in [0, 1), by the fixed evaluation described above."""
+    u = np.asarray(u, np.float32)
+    t = u * _F(4.0)
+    o = np.floor(t)
+    f = t - o
+    o = o.astype(np.int64)
+    x = f * _HALF_PI
+    x2 = x * x
+    q = x2 * _SIN_C[0] + _SIN_C[1]
+    for c in _SIN_C[2:]:
+        q = q * x2 + c
+    q = q * x2
+    sn = x + x * q
+    r = x2 * _COS_C[0] + _COS_C[1]
+    for c in _COS_C[2:]:
+        r = r * x2 + c
+    r = r * x2
+    cs = _F(1.0) + r
+    c_out = np.select([o == 0, o == 1, o == 2], [cs, -sn, -cs], sn)
+    s_out = np.select([o == 0, o == 1, o == 2], [sn, cs, -sn], -cs)
+    return c_out.astype(np.float32), s_out.astype(np.float32)
 
 
 def m_flat_index(q, k, I, a, b, nk, ni, nb):
@@ -109,20 +162,25 @@ def m_values_from_index(idx, seed, nb):
     """Complex Gaussian M values for flat indices idx (uint64 array).
 
     counter = (idx mod 2^32, idx div 2^32, STREAM_M, 0), key = (seed lo, seed hi);
-    u1 in (0,1], u2 in [0,1) from 53-bit mantissas; Box-Muller
-    r = sqrt(-2 ln u1), theta = TWO_PI * u2; M = (r cos theta + i r sin theta) / sqrt(2 nb).
+    24-bit uniforms u1 = (x0 >> 8) + 1) 2^-24 in (0, 1] and u2 = (x1 >> 8) 2^-24 in [0, 1) from the
+    first two output words; Box-Muller in FP32: r = sqrt(-2 ln u1), (c, s) = (cos, sin)(2 pi u2)
+    (log_f32, sincos_turn_f32), re = r c and im = r s rounded to FP32; M = (re + i im) sqrt(1/(2 nb))
+    with the last product in FP64. E|M|^2 = 1/nb.
     """
     idx = np.asarray(idx, dtype=np.uint64)
-    x0, x1, x2, x3 = philox4x32_10(idx & _MASK32, idx >> _S32,
-                                   np.full(idx.shape, STREAM_M, np.uint64),
-                                   np.zeros(idx.shape, np.uint64),
-                                   seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
-    u1 = _u53_open0(x0, x1)
-    u2 = _u53(x2, x3)
-    r = np.sqrt(-2.0 * np.log(u1))
-    th = TWO_PI * u2
-    s = math.sqrt(0.5 / nb)
-    return (r * np.cos(th)) * s + 1j * ((r * np.sin(th)) * s)
+    x0, x1, _, _ = philox4x32_10(idx & _MASK32, idx >> _S32,
+                                 np.full(idx.shape, STREAM_M, np.uint64),
+                                 np.zeros(idx.shape, np.uint64),
+                                 seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    u1 = ((x0 >> np.uint64(8)).astype(np.float32) + _F(1.0)) * _F(2.0 ** -24)
+    u2 = (x1 >> np.uint64(8)).astype(np.float32) * _F(2.0 ** -24)
+    w = log_f32(u1) * _F(-2.0)
+    r = np.sqrt(w)
+    c, s = sincos_turn_f32(u2)
+    re = (r * c).astype(np.float64)
+    im = (r * s).astype(np.float64)
+    sc = math.sqrt(0.5 / nb)
+    return re * sc + 1j * (im * sc)
 
 
 def m_block(seed, q, k, nk, ni, nb):

@@ -55,7 +55,14 @@ gw_status check_launch(gw_ctx* c, const char* what) {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) and Box-Muller: synthetic
 // matrix elements M^I_ab(k, q) with E|M|^2 = 1/nb (stand-in for Eq. mmatrix).
 // counter = (idx lo, idx hi, 0x4D, 0), key = (seed lo, seed hi), idx the flat
-// index of (q, k, I, a, b); u1 = (m1 + 1) 2^-53, u2 = m2 2^-53 from 53-bit words.
+// index of (q, k, I, a, b); 24-bit uniforms u1 = ((x0 >> 8) + 1) 2^-24, u2 = (x1 >> 8) 2^-24.
+// Box-Muller in FP32 with the logarithm and the sine / cosine of the generator's definition:
+// fixed sequences of explicitly round-to-nearest FP32 operations (no contraction into FMAs), so
+// the values are bit-identical to the host generator's.
+//   ln u: u = 2^e m, m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s), s = (m - 1)/(m + 1), by the
+//         odd series to s^11; ln u = e ln 2 + ln m.
+//   cos / sin (2 pi u): quadrant o and f = 4 u - o exactly; x = (pi/2) f; Taylor series of sin x
+//         to x^13 and of cos x to x^12; the quadrant by exact sign and order changes.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
                                               uint32_t k0, uint32_t k1) {
@@ -73,22 +80,67 @@ __device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32
   }
 }
 
+// series coefficients 1/k and (-1)^(k/2) / k! rounded to FP32 (as the host generator rounds them)
+__constant__ float c_atanh[5] = {(float)(1.0 / 11), (float)(1.0 / 9), (float)(1.0 / 7), (float)(1.0 / 5),
+                                 (float)(1.0 / 3)};
+__constant__ float c_sin[6] = {(float)(1.0 / 6227020800.0), (float)(-1.0 / 39916800.0), (float)(1.0 / 362880.0),
+                               (float)(-1.0 / 5040.0), (float)(1.0 / 120.0), (float)(-1.0 / 6.0)};
+__constant__ float c_cos[6] = {(float)(1.0 / 479001600.0), (float)(-1.0 / 3628800.0), (float)(1.0 / 40320.0),
+                               (float)(-1.0 / 720.0), (float)(1.0 / 24.0), (float)(-1.0 / 2.0)};
+
+__device__ __forceinline__ float gen_log(float u) {
+  const uint32_t bits = __float_as_uint(u);
+  int e = (int)((bits >> 23) & 255u) - 126;
+  float m = __uint_as_float((bits & 0x7FFFFFu) | (126u << 23));  // u = m 2^e, m in [0.5, 1)
+  if (m < (float)0.7071067811865476) {
+    m = __fmul_rn(m, 2.0f);
+    e -= 1;
+  }
+  const float f = __fsub_rn(m, 1.0f);
+  const float s = __fdiv_rn(f, __fadd_rn(2.0f, f));
+  const float z = __fmul_rn(s, s);
+  float p = __fadd_rn(__fmul_rn(z, c_atanh[0]), c_atanh[1]);
+#pragma unroll
+  for (int i = 2; i < 5; ++i) p = __fadd_rn(__fmul_rn(p, z), c_atanh[i]);
+  p = __fmul_rn(p, z);
+  const float s2 = __fadd_rn(s, s);
+  const float lm = __fadd_rn(s2, __fmul_rn(s2, p));
+  return __fadd_rn(__fmul_rn((float)e, (float)0.6931471805599453), lm);
+}
+
+__device__ __forceinline__ void gen_sincos_turn(float u, float& c, float& s) {
+  const float t = __fmul_rn(u, 4.0f);
+  const float of = floorf(t);
+  const float f = __fsub_rn(t, of);
+  const int o = (int)of;
+  const float x = __fmul_rn(f, (float)1.5707963267948966);
+  const float x2 = __fmul_rn(x, x);
+  float q = __fadd_rn(__fmul_rn(x2, c_sin[0]), c_sin[1]);
+#pragma unroll
+  for (int i = 2; i < 6; ++i) q = __fadd_rn(__fmul_rn(q, x2), c_sin[i]);
+  q = __fmul_rn(q, x2);
+  const float sn = __fadd_rn(x, __fmul_rn(x, q));
+  float r = __fadd_rn(__fmul_rn(x2, c_cos[0]), c_cos[1]);
+#pragma unroll
+  for (int i = 2; i < 6; ++i) r = __fadd_rn(__fmul_rn(r, x2), c_cos[i]);
+  r = __fmul_rn(r, x2);
+  const float cs = __fadd_rn(1.0f, r);
+  c = o == 0 ? cs : (o == 1 ? -sn : (o == 2 ? -cs : sn));
+  s = o == 0 ? sn : (o == 1 ? cs : (o == 2 ? -sn : -cs));
+}
+
 __global__ void k_gen_m(double2* __restrict__ M, uint64_t n, uint64_t off, uint64_t seed, double scale) {
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < n;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t ctr = idx + off;
     uint32_t c0 = (uint32_t)ctr, c1 = (uint32_t)(ctr >> 32), c2 = 0x4Du, c3 = 0u;
     philox4x32_10(c0, c1, c2, c3, (uint32_t)seed, (uint32_t)(seed >> 32));
-    const uint64_t m1 = ((uint64_t)c0 << 21) | (c1 >> 11);
-    const uint64_t m2 = ((uint64_t)c2 << 21) | (c3 >> 11);
-    const double u1 = ((double)m1 + 1.0) * 0x1p-53;
-    const double u2 = (double)m2 * 0x1p-53;
-    const double r = sqrt(-2.0 * log(u1));
-    // theta = 2 pi u2; sincospi takes theta / pi = 2 u2 exactly (no range reduction by pi),
-    // which differs from rounding 2 pi u2 first by < 1e-15
-    double s, co;
-    sincospi(2.0 * u2, &s, &co);
-    M[idx] = make_double2(r * co * scale, r * s * scale);
+    const float u1 = __fmul_rn(__fadd_rn(__uint2float_rn(c0 >> 8), 1.0f), 0x1p-24f);
+    const float u2 = __fmul_rn(__uint2float_rn(c1 >> 8), 0x1p-24f);
+    const float r = __fsqrt_rn(__fmul_rn(gen_log(u1), -2.0f));
+    float co, sn;
+    gen_sincos_turn(u2, co, sn);
+    M[idx] = make_double2((double)__fmul_rn(r, co) * scale, (double)__fmul_rn(r, sn) * scale);
   }
 }
 
