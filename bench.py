@@ -479,6 +479,71 @@ def run_offdiag(args):
     ctx.close()
 
 
+def run_gap_check(args):
+    """The metric's accuracy claim on the benchmarked crystal (nk64_nb64, all 64 q): one G0W0 iteration
+    in FP64 (every step FP64) and in the mixed form (tensor-core P and Sigma^c, float-float or FP32
+    dielectric solve), the same continuation applied to both: CPE at ridges 1e-3, 1e-4, 1e-5 and Pade.
+    Reports each chain's quasiparticle gap, the gap differences and the largest QP-energy difference
+    (meV), the |Sigma| scale and the FP64 iteration time. A measurement run, not a bench line."""
+    import torch
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    from paper_1602_02313_gb300.driver import Chain, cpe_grid
+    b.build()
+    cr, gr = gi.make_config(args.gap_config)
+    if args.nq > 0:
+        cr = gi.subset_q(cr, 0, min(args.nq, cr.nq))
+    ctx = gw.GW(gr, cr, omega=args.omega)
+    eps = torch.from_numpy(cr.eps).cuda()
+    HA_MEV = 27211.386245988
+    ridges = (1e-3, 1e-4, 1e-5)
+    variants = [("fp64", gw.GW_FP64, gw.GW_FP64), ("mixed_f32x2", gw.GW_FP16X2, gw.GW_F32X2),
+                ("mixed_f32", gw.GW_FP16X2, gw.GW_F32)]
+    res, eq = {}, {}
+    for name, prec, sprec in variants:
+        ch = Chain(ctx, eps, prec=prec, qb=min(64, cr.nq), cont_method=gw.GW_CPE, screen_prec=sprec)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        ch.step()
+        e1.record(st)
+        ch.check()
+        r = {"iteration_ms": e0.elapsed_time(e1), "sigx_max_abs_ha": float(ch.Sx.abs().max()),
+             "sigc_iw0_max_abs_ha": float(ch.Siwc[:, :, 0].abs().max())}
+        for ridge in ridges:
+            ctx.cpe_setup(cpe_grid(), ridge)
+            ch.cont_method = gw.GW_CPE
+            ch.finish(ch.vxc)
+            ch.check()
+            e = ch.eqp.cpu().numpy().reshape(cr.nk, cr.nb).copy()
+            eq[(name, f"cpe_{ridge:g}")] = e
+            r[f"gap_cpe_{ridge:g}_ha"] = float(e[:, cr.nocc].min() - e[:, cr.nocc - 1].max())
+        ch.cont_method = gw.GW_PADE
+        ch.finish(ch.vxc)
+        ch.check()
+        e = ch.eqp.cpu().numpy().reshape(cr.nk, cr.nb).copy()
+        eq[(name, "pade")] = e
+        r["gap_pade_ha"] = float(e[:, cr.nocc].min() - e[:, cr.nocc - 1].max())
+        res[name] = r
+        del ch
+        torch.cuda.empty_cache()
+    diffs = {}
+    for name in ("mixed_f32x2", "mixed_f32"):
+        for cont in [f"cpe_{x:g}" for x in ridges] + ["pade"]:
+            g_m, g_f = res[name][f"gap_{cont}_ha"], res["fp64"][f"gap_{cont}_ha"]
+            d = eq[(name, cont)] - eq[("fp64", cont)]
+            diffs[f"{name}/{cont}"] = {"gap_err_mev": (g_m - g_f) * HA_MEV,
+                                       "max_abs_qp_err_mev": float(np.abs(d).max() * HA_MEV),
+                                       "median_abs_qp_err_mev": float(np.median(np.abs(d)) * HA_MEV)}
+    out = {"metric": "quasiparticle gap, mixed vs FP64 chain (one G0W0 iteration)", "config": args.gap_config,
+           "nq": cr.nq, "omega": args.omega, "vxc": "Sigma^x[G0]", "chains": res, "differences": diffs}
+    print(json.dumps(out))
+    ctx.close()
+
+
 def run_dyson_matrix(args):
     """Full-matrix Dyson update (gw_dyson_matrix, FP64) at the nk64_nb64 band and grid sizes: Nk = 64,
     Nb = 64, Ntau = Nw = 48, beta = 200; a Hermitian static part and a Hermitian Sigma^c(tau) made of
@@ -575,6 +640,7 @@ def main():
     ap.add_argument("--cont", default="cpe_mlp", choices=["cpe_mlp", "cpe", "pade"],
                     help="continuation: CPE warm-started by the learned seed (default), plain CPE, or Pade")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--gap-config", default="nk64_nb64", help="crystal of --config gapcheck")
     args = ap.parse_args()
     if args.omega is None:
         import gwinputs as gi
@@ -589,6 +655,8 @@ def main():
         return run_offdiag(args)
     if args.config == "dyson_matrix":
         return run_dyson_matrix(args)
+    if args.config == "gapcheck":
+        return run_gap_check(args)
     if args.config == "sym":
         import paper_1602_02313_gb300 as gw
         return run_sym(args, gw.PREC[args.prec])
