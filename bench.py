@@ -544,6 +544,68 @@ def run_gap_check(args):
     ctx.close()
 
 
+def run_mlp(args):
+    """The learned CPE seed at its stated scale: ~2e5 band-diagonal Sigma^c(i w) samples from the G0W0
+    chains of 48 synthetic crystals shaped like the benchmarked one (Nk = 64, Nb = 64, NI = 256,
+    Ntau = 48; seeds apart from it), GPU training (tensor-core forward, backward and Adam), then on two
+    held-out crystals of the same shape the QP energies of the seeded CPE fit against the plain CPE
+    fit and Pade, with the Lawson-Hanson iterations and the continuation time. A measurement run."""
+    import torch
+
+    import gwinputs as gi
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    from paper_1602_02313_gb300 import learned
+    from paper_1602_02313_gb300.driver import Chain
+    b.build()
+    HA_MEV = 27211.386245988
+    mk = lambda s: gi.make_config("nk64_nb64", seed=s)  # noqa: E731
+    t0 = time.perf_counter()
+    x, A = learned.chain_samples(mk, list(range(9101, 9101 + args.mlp_crystals)), args.omega, qb=64)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = gw.MLP(seed=17)
+    t0 = time.perf_counter()
+    hist = learned.train(net, x, A, steps=args.mlp_steps, batch=1024, lr=3e-4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    held = []
+    for s in (9301, 9302):
+        cr, gr = mk(s)
+        ctx = gw.GW(gr, cr, omega=args.omega)
+        ch = Chain(ctx, torch.from_numpy(cr.eps).cuda(), prec=gw.GW_FP16X2, qb=64, cont_method=gw.GW_CPE)
+        ch.start_g0()
+        ch.sigma()
+        ch.finish()
+        ch.check()
+        r = learned.continuation_gain(ctx, net, ch)
+        bsol = torch.zeros(cr.nk * cr.nb, len(ch.cpe_x) - 2, dtype=torch.float64, device="cuda")
+        ctx.cpe_coeffs(bsol)
+        supp = (bsol > 0).sum(1).float()
+        ds = np.abs(r["e_seeded"] - r["e_plain"]) * HA_MEV
+        dp = np.abs(r["e_pade"] - r["e_plain"]) * HA_MEV
+        dsp = np.abs(r["e_seeded"] - r["e_pade"]) * HA_MEV
+        gap = lambda e: float((e.reshape(cr.nk, cr.nb)[:, cr.nocc].min()  # noqa: E731
+                               - e.reshape(cr.nk, cr.nb)[:, cr.nocc - 1].max()) * HA_MEV)
+        held.append({"seed": s, "solution_support_mean": float(supp.mean()),
+                     "nnls_iterations_plain_mean": float(r["iters_plain"].mean()),
+                     "nnls_iterations_seeded_mean": float(r["iters_seeded"].mean()),
+                     "continuation_ms_plain": r["ms_plain"], "continuation_ms_seeded": r["ms_seeded"],
+                     "continuation_ms_pade": r["ms_pade"],
+                     "qp_seeded_vs_plain_cpe_mev": {"max": float(ds.max()), "median": float(np.median(ds))},
+                     "qp_pade_vs_plain_cpe_mev": {"max": float(dp.max()), "median": float(np.median(dp))},
+                     "qp_seeded_vs_pade_mev": {"max": float(dsp.max()), "median": float(np.median(dsp))},
+                     "gap_mev": {"plain_cpe": gap(r["e_plain"]), "seeded_cpe": gap(r["e_seeded"]),
+                                 "pade": gap(r["e_pade"])}})
+        ctx.close()
+    out = {"metric": "learned CPE seed: training at scale and its gain over the plain continuation",
+           "samples": int(x.shape[0]), "crystals": args.mlp_crystals, "data_s": t_data, "train_s": t_train,
+           "train_steps": args.mlp_steps, "batch": 1024, "lr": 3e-4, "loss_first": hist[0], "loss_last": hist[-1],
+           "loss_history_every_50": hist, "held_out": held}
+    print(json.dumps(out))
+    net.close()
+
+
 def run_dyson_matrix(args):
     """Full-matrix Dyson update (gw_dyson_matrix, FP64) at the nk64_nb64 band and grid sizes: Nk = 64,
     Nb = 64, Ntau = Nw = 48, beta = 200; a Hermitian static part and a Hermitian Sigma^c(tau) made of
@@ -641,6 +703,8 @@ def main():
                     help="continuation: CPE warm-started by the learned seed (default), plain CPE, or Pade")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--gap-config", default="nk64_nb64", help="crystal of --config gapcheck")
+    ap.add_argument("--mlp-crystals", type=int, default=48, help="training crystals of --config mlp")
+    ap.add_argument("--mlp-steps", type=int, default=4000, help="training steps of --config mlp")
     args = ap.parse_args()
     if args.omega is None:
         import gwinputs as gi
@@ -657,6 +721,8 @@ def main():
         return run_dyson_matrix(args)
     if args.config == "gapcheck":
         return run_gap_check(args)
+    if args.config == "mlp":
+        return run_mlp(args)
     if args.config == "sym":
         import paper_1602_02313_gb300 as gw
         return run_sym(args, gw.PREC[args.prec])

@@ -14,7 +14,7 @@ from .driver import Chain
 NFIT = 64  # Matsubara points fed to the network: 2 x 64 = 128 inputs
 
 
-def chain_samples(make_crystal_grid, seeds, omega, prec=GW_FP16X2):
+def chain_samples(make_crystal_grid, seeds, omega, prec=GW_FP16X2, qb=4):
     """Network inputs x [N][2 NFIT] (float32, device) from the Sigma^c(i w) of G0W0 chains,
     one crystal per seed (make_crystal_grid(seed) -> (crystal, grid))."""
     xs = []
@@ -22,7 +22,7 @@ def chain_samples(make_crystal_grid, seeds, omega, prec=GW_FP16X2):
     for s in seeds:
         cr, gr = make_crystal_grid(s)
         ctx = GW(gr, cr, omega=omega)
-        ch = Chain(ctx, torch.from_numpy(cr.eps).cuda(), prec=prec, qb=4, cont_method=GW_CPE)
+        ch = Chain(ctx, torch.from_numpy(cr.eps).cuda(), prec=prec, qb=qb, cont_method=GW_CPE)
         ch.start_g0()
         ch.sigma()
         ch.finish()
@@ -81,3 +81,44 @@ def trained_seed(omega, seeds=(9001, 9002, 9003), steps=400, device=0):
     net = MLP(seed=17, device=device)
     hist = train(net, x, A, steps=steps, batch=512, lr=1e-3)
     return net, hist
+
+
+def continuation_gain(ctx, mlp, chain, reps=3):
+    """On one chain's Sigma^c: QP energies and timing of the plain CPE fit, the CPE fit seeded by the
+    network, and Pade, all through gw_continue. Returns a dict of host arrays and timings (ms, the
+    best of reps; the seeded time includes the features, the network and the seed)."""
+    from . import GW_PADE
+    nprob = chain.nk * chain.nb
+    vxc = chain.Sx.reshape(-1)
+    eps, sx = chain.eps.reshape(-1), chain.Sx.reshape(-1)
+    st = ctx.stream
+    out = {}
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    def plain():
+        ctx.continue_(GW_CPE, chain.Siwc, eps, sx, vxc, None, None, chain.eqp, chain.qinfo)
+
+    out["ms_plain"] = timed(plain)
+    it = torch.zeros(nprob, dtype=torch.int32, device="cuda")
+    ctx.cpe_iterations(it)
+    out["iters_plain"] = it.cpu().numpy()
+    out["e_plain"] = chain.eqp.cpu().numpy().copy()
+    out["ms_seeded"] = timed(lambda: seeded_cpe(ctx, mlp, chain))
+    ctx.cpe_iterations(it)
+    out["iters_seeded"] = it.cpu().numpy()
+    out["e_seeded"] = chain.eqp.cpu().numpy().copy()
+    out["ms_pade"] = timed(lambda: ctx.continue_(GW_PADE, chain.Siwc, eps, sx, vxc, None, None, chain.eqp,
+                                                 chain.qinfo))
+    out["e_pade"] = chain.eqp.cpu().numpy().copy()
+    return out

@@ -19,11 +19,17 @@ def gw():
 
 
 def test_mlp_gradients_vs_oracle(gw):
+    """Loss and gradients of the tensor-core network against the FP64 oracle network. The weights,
+    the inputs and the CPE matrix are made exactly representable in fp16, so that the operand
+    rounding of the first products is exact; what remains is the fp16 rounding of the hidden
+    activations the kernels keep for the next product (2^-11 relative) and FP32 accumulation."""
     import torch
     net = gw.MLP(seed=3)
     rng = np.random.default_rng(7)
-    x = (0.5 * rng.standard_normal((256, 128))).astype(np.float32)
-    A = (0.05 * rng.standard_normal((128, 128))).astype(np.float32)
+    f16 = lambda a: np.asarray(a, np.float32).astype(np.float16).astype(np.float32)  # noqa: E731
+    net.set_params(f16(net.get_params()))
+    x = f16(0.5 * rng.standard_normal((256, 128)))
+    A = f16(0.05 * rng.standard_normal((128, 128)))
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     grads = torch.zeros(net.num_params(), dtype=torch.float32, device="cuda")
     net.loss_grad(torch.from_numpy(x).cuda(), torch.from_numpy(A).cuda(), loss, grads)
@@ -38,7 +44,9 @@ def test_mlp_gradients_vs_oracle(gw):
         off += dout
     ref_loss, ref = omlp.loss_and_grad(params, x.astype(np.float64), A.astype(np.float64))
     g = grads.cpu().numpy().astype(np.float64)
-    assert abs(float(loss.item()) - ref_loss) < 1e-2 * ref_loss
+    eL = abs(float(loss.item()) - ref_loss) / ref_loss
+    print(f"loss rel err {eL:.2e}")
+    assert eL < 1e-3
     off = 0
     for l, (gW, gb) in enumerate(ref):
         GW_ = g[off:off + gW.size].reshape(gW.shape)
@@ -48,8 +56,8 @@ def test_mlp_gradients_vs_oracle(gw):
         eW = np.linalg.norm(GW_ - gW) / np.linalg.norm(gW)
         eb = np.linalg.norm(Gb - gb) / max(np.linalg.norm(gb), 1e-30)
         print(f"layer {l}: |dW| rel err {eW:.2e}, |db| rel err {eb:.2e}")
-        # fp16 operands (11-bit significand) with FP32 accumulation
-        assert eW < 3e-2 and eb < 3e-2
+        # fp16 hidden activations (11-bit significand) with FP32 accumulation
+        assert eW < 1e-3 and eb < 1e-3
     net.close()
 
 
