@@ -191,8 +191,10 @@ def _dtype(args):
 
 def run_batch(args, prec):
     """Twelve heterogeneous crystals (gwinputs.batch_crystals): one GW iteration of all of them
-    launched call by call, crystal after crystal, against one replay of the autotuned CUDA graph.
-    Not the headline workload; one GPU."""
+    launched call by call, crystal after crystal, against one replay of the autotuned CUDA graph of
+    per-crystal branches and one replay of the queued graph (per q index, one persistent
+    polarization launch whose blocks pull units of every crystal from a device counter). Not the
+    headline workload; one GPU."""
     import torch
 
     import gwinputs as gi
@@ -207,13 +209,21 @@ def run_batch(args, prec):
     sched = batch.tune_schedule(branch_choices=(1, 2, 3, 4, 6, 12), reps=1)
     graph_ms = batch.time_graph(batch.graph, reps=args.steps)
     batch.check()
+    # the queued schedule: per q index one persistent polarization launch over all crystals
+    batch.step_queued()
+    batch.check()
+    gq = batch.capture_queued()
+    queued_ms = batch.time_graph(gq, reps=args.steps)
+    batch.check()
+    best_ms = min(graph_ms, queued_ms)
     shapes = [f"Nk={cr.nk} Nb={cr.nb} NI={cr.ni} Ntau={len(gr.tau)} beta={gr.beta}" for cr, gr in systems]
-    out = {"metric": METRIC + " (batch of 12 crystals)", "value": batch.flops / (graph_ms * 1e-3) / 1e12,
-           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": graph_ms,
+    out = {"metric": METRIC + " (batch of 12 crystals)", "value": batch.flops / (best_ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best_ms,
            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "fp16x2 split (fp32 accum) + f64",
            "data": "synthetic",
            "config": {"workload": "batch of 12 heterogeneous synthetic crystals: " + "; ".join(shapes),
-                      "sequential_ms": seq_ms, "graph_ms": graph_ms, "speedup_vs_sequential": seq_ms / graph_ms,
+                      "sequential_ms": seq_ms, "graph_ms": graph_ms, "queued_graph_ms": queued_ms,
+                      "speedup_vs_sequential": seq_ms / best_ms,
                       "branches": batch.nbranch, "graph_ms_by_branches": sched,
                       "crystal_ms": crystal_ms, "pol_tuning": tuning, "continuation": "cpe",
                       "l2": "inputs larger than L2"},
@@ -606,6 +616,103 @@ def run_mlp(args):
     net.close()
 
 
+def run_c3(args):
+    """The nk216_nb128 workload as a whole: all 216 q of the Nk = 216 (6x6x6), Nb = 128 (48
+    occupied), NI = 512, Ntau = Nnu = Nw = 64, beta = 400 crystal, mixed precision (tensor-core P and
+    Sigma^c, float-float screening and bosonic transforms), one G0W0 iteration and args.c3_passes
+    self-consistent passes (P, W~ and Sigma from the previous pass's dressed G), CPE continuation.
+    Prints one JSON line per pass (time, gap, the change of G) and, first, per-quantity errors of
+    this precision at sampled points: P of one q at two tau and Sigma^c of that q at sampled (k, tau)
+    (with a Hermitian stand-in for W~(tau)) against the FP64 oracle, and the float-float dielectric
+    solve of that q against the FP64 one on the GPU. A measurement run."""
+    import torch
+
+    import gwinputs as gi
+    import oracle as orc
+    import paper_1602_02313_gb300 as gw
+    from paper_1602_02313_gb300 import build as b
+    from paper_1602_02313_gb300.driver import Chain, contraction_flops
+    b.build()
+    HA_MEV = 27211.386245988
+    cr, gr = gi.make_config("nk216_nb128")
+    if args.nq > 0:
+        cr = gi.subset_q(cr, 0, min(args.nq, cr.nq))
+    ctx = gw.GW(gr, cr, omega=args.omega)
+    eps = torch.from_numpy(cr.eps).cuda()
+    d = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()  # noqa: E731
+    # ---- per-quantity errors at sampled points, one q
+    iq = 7 % cr.nq
+    its, ks = [0, 37], [0, 215 % cr.nk]
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    P = torch.zeros((gr.ntau, cr.ni, cr.ni), dtype=torch.complex128, device="cuda")
+    ctx.polarization(iq, d(G), P, gw.GW_FP16X2)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((gr.ntau, cr.ni, 8)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 8))
+    Wst = -30.0 * (X @ np.conj(np.swapaxes(X, 1, 2))) / 8
+    S1 = torch.zeros((cr.nk, cr.nb, gr.ntau), dtype=torch.float64, device="cuda")
+    ctx.selfenergy(iq, d(G), d(occ), d(Wst), S1, None, gw.GW_FP16X2)
+    Piv = torch.zeros((1, gr.nnu, cr.ni, cr.ni), dtype=torch.complex128, device="cuda")
+    ctx.tau_to_freq_many(gw.GW_BOSE, gw.GW_TAU_TO_IW, 1, cr.ni * cr.ni, P, Piv, gw.GW_F32X2)
+    Wff, W64 = torch.zeros_like(Piv), torch.zeros_like(Piv)
+    inf = torch.zeros((1, gr.nnu), dtype=torch.int32, device="cuda")
+    ctx.screen(iq, 1, Piv, Wff, inf, gw.GW_F32X2)
+    ctx.screen(iq, 1, Piv, W64, inf, gw.GW_FP64)
+    ctx.sync()
+    t0 = time.perf_counter()
+    # the oracle's P of q at the tau indices its_p, its sum over k taken in chunks of 8 k (M of all
+    # 216 k would take 29 GB of host memory): each chunk is the oracle's polarization of those k
+    # (their G rows first, then all rows for k - q), weighted by chunk size / Nk
+    its_p = its[1:]
+    Pr = 0.0
+    for k0 in range(0, cr.nk, 8):
+        kk = list(range(k0, min(cr.nk, k0 + 8)))
+        Mk = gi.m_for_q(cr, iq, ks=kk)
+        Gx = np.concatenate([G[kk], G])
+        Pr = Pr + orc.polarization(Mk, Gx, cr.kmq[iq][kk] + len(kk), omega=args.omega, its=its_p) * (len(kk) / cr.nk)
+    Mk = gi.m_for_q(cr, iq, ks=ks)
+    Sr, _, _ = orc.selfenergy(Mk, G, Wst, cr.v[iq], cr.kmq[iq], occ, omega=args.omega, ks=ks, its=its)
+    t_orc = time.perf_counter() - t0
+    rel = lambda a, b_: float(np.abs(a - b_).max() / np.abs(b_).max())  # noqa: E731
+    Sg = S1.cpu().numpy()
+    errs = {"P_tc_vs_oracle": rel(P.cpu().numpy()[its_p], Pr),
+            "Sigma_c_tc_vs_oracle": max(rel(Sg[k][:, its], Sr[k][:, its]) for k in ks),
+            "W_f32x2_vs_fp64_gpu": rel(Wff.cpu().numpy(), W64.cpu().numpy()),
+            "sample": f"q {iq}; P at tau index {its_p}; Sigma^c at k {ks} x tau {its} with a Hermitian stand-in "
+                      f"for W~(tau); the dielectric solve at all {gr.nnu} nu of q {iq}", "oracle_s": t_orc}
+    print(json.dumps({"c3": "errors", **errs}), flush=True)
+    del P, Piv, Wff, W64, S1
+    torch.cuda.empty_cache()
+    # ---- the chain
+    ch = Chain(ctx, eps, prec=gw.GW_FP16X2, qb=32, cont_method=gw.GW_CPE)
+    fp, fs = contraction_flops(cr.nk, cr.nb, cr.ni, gr.ntau)
+    flops = (fp + fs) * cr.nq
+    st = torch.cuda.current_stream()
+
+    def gap(e):
+        e = e.cpu().numpy().reshape(cr.nk, cr.nb)
+        return float((e[:, cr.nocc].min() - e[:, cr.nocc - 1].max()) * HA_MEV)
+
+    Gprev = None
+    for it in range(args.c3_passes + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        if it == 0:
+            ch.step()
+        else:
+            ch.iterate(1)
+        e1.record(st)
+        ch.check()
+        ms = e0.elapsed_time(e1)
+        dG = None if Gprev is None else float((ch.G1 - Gprev).abs().max() / ch.G1.abs().max())
+        Gprev = ch.G1.clone()
+        print(json.dumps({"c3": "pass", "pass": it, "kind": "G0W0" if it == 0 else "scGW", "ms": ms,
+                          "tflops_algorithmic": flops / (ms * 1e-3) / 1e12, "gap_mev": gap(ch.eqp),
+                          "max_rel_change_G": dG, "sigx_max_abs_ha": float(ch.Sx.abs().max()),
+                          "qp_not_converged": int((ch.qinfo != 0).sum())}), flush=True)
+    ctx.close()
+
+
 def run_dyson_matrix(args):
     """Full-matrix Dyson update (gw_dyson_matrix, FP64) at the nk64_nb64 band and grid sizes: Nk = 64,
     Nb = 64, Ntau = Nw = 48, beta = 200; a Hermitian static part and a Hermitian Sigma^c(tau) made of
@@ -704,6 +811,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--gap-config", default="nk64_nb64", help="crystal of --config gapcheck")
     ap.add_argument("--mlp-crystals", type=int, default=48, help="training crystals of --config mlp")
+    ap.add_argument("--c3-passes", type=int, default=8, help="self-consistent passes of --config c3run")
     ap.add_argument("--mlp-steps", type=int, default=4000, help="training steps of --config mlp")
     args = ap.parse_args()
     if args.omega is None:
@@ -723,6 +831,8 @@ def main():
         return run_gap_check(args)
     if args.config == "mlp":
         return run_mlp(args)
+    if args.config == "c3run":
+        return run_c3(args)
     if args.config == "sym":
         import paper_1602_02313_gb300 as gw
         return run_sym(args, gw.PREC[args.prec])

@@ -135,6 +135,20 @@ gw_status gw_green_tau(gw_ctx* ctx, const double* eps, const double* sigx, const
  * G_tau [nk][nb][ntau] (any G: G0 or dressed); P_tau out cplx [ntau][ni][ni] (Hermitian). */
 gw_status gw_polarization(gw_ctx* ctx, int iq, const double* G_tau, gw_prec prec, double* P_tau);
 
+/* The polarization of several crystals (one q each) in one persistent launch: job j is
+ * gw_polarization(ctxs[j], iqs[j], G_tau[j], prec, P_tau[j]), with the same results bit for bit.
+ * All work runs on ctxs[0]'s stream (order the other contexts' earlier work before it). Each job's
+ * operand image and pair weights are built first; then one thread block per SM pulls work units
+ * (job, K segment, strip, tau) from a device counter until all are taken, so that the units of
+ * small crystals fill the GPU beside those of large ones (the batched heterogeneous workload);
+ * then each job's partials are summed into its P. ctxs, iqs, G_tau, P_tau are HOST arrays of
+ * njobs entries (G_tau[j], P_tau[j] device pointers as in gw_polarization). 1 <= njobs <= 16,
+ * every context at most once and all on one device, else GW_EINVAL; prec GW_FP16X2 only, else
+ * GW_EUNSUPPORTED. A device wait that runs out is reported by gw_sync(ctxs[0]). No host-device
+ * copy: the call can be captured into a CUDA graph once every context has run one polarization. */
+gw_status gw_polarization_many(int njobs, gw_ctx* const* ctxs, const int* iqs, const double* const* G_tau,
+                               double* const* P_tau, gw_prec prec);
+
 /* Imaginary time <-> Matsubara transforms (Eq. trans and its bosonic / inverse
  * counterparts), fixed matrices (built in extended precision, stored FP64) applied as
  * batched matvecs. prec: GW_FP64 (native FP64), or GW_F32X2 for the two bosonic

@@ -31,7 +31,7 @@ _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW
            -5: "GW_ENOCONV", -6: "GW_ETIMEOUT", -7: "GW_EUNSUPPORTED"}
 
 # Every symbol declared in include/gw.h.
-EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization",
+EXPORTS = ["gw_create", "gw_destroy", "gw_sync", "gw_last_error", "gw_green_tau", "gw_polarization", "gw_polarization_many",
            "gw_tau_to_freq", "gw_tau_to_freq_many", "gw_screen", "gw_screen_tau", "gw_dyson_tau", "gw_sigma_star", "gw_selfenergy_offdiag", "gw_dyson_matrix", "gw_selfenergy", "gw_continue", "gw_cpe_setup",
            "gw_cpe_coeffs", "gw_copy_m", "gw_transform_matrices", "gw_launch_count",
            "gw_kernel_timing", "gw_kernel_time", "gw_set_stream", "gw_set_tuning", "gw_measure_alu",
@@ -100,6 +100,20 @@ def transform_matrices(grid):
             "F_bwd_re": fb[:, :nw], "F_bwd_im": fb[:, nw:]}
 
 
+def polarization_many(ctxs, iqs, Gs, Ps, prec=GW_FP16X2):
+    """gw_polarization_many: the polarization of several contexts (one q each) in one persistent
+    launch on ctxs[0]'s stream. ctxs: GW objects; iqs: q indices; Gs, Ps: device tensors."""
+    n = len(ctxs)
+    H = (ctypes.c_void_p * n)(*[c.h for c in ctxs])
+    Q = (ctypes.c_int * n)(*[int(q) for q in iqs])
+    G = (ctypes.c_void_p * n)(*[_ptr(g).value for g in Gs])
+    P = (ctypes.c_void_p * n)(*[_ptr(p).value for p in Ps])
+    st = lib().gw_polarization_many(n, H, Q, G, P, int(prec))
+    if st != GW_OK:
+        msg = lib().gw_last_error(ctxs[0].h)
+        raise GwError(f"gw_polarization_many: {_STATUS.get(st, st)}: {msg.decode() if msg else ''}")
+
+
 def load_library(path=LIB_PATH):
     """Load libgw.so and declare argument types; raises if it is missing."""
     if not os.path.exists(path):
@@ -111,6 +125,7 @@ def load_library(path=LIB_PATH):
         "gw_destroy": [vp], "gw_sync": [vp], "gw_last_error": [vp],
         "gw_green_tau": [vp, vp, vp, vp, vp, vp, vp],
         "gw_polarization": [vp, i32, vp, i32, vp],
+        "gw_polarization_many": [i32, vp, vp, vp, vp, i32],
         "gw_tau_to_freq": [vp, i32, i32, i64, vp, i32, vp],
         "gw_tau_to_freq_many": [vp, i32, i32, i32, i64, vp, i32, vp],
         "gw_screen_tau": [vp, i32, i32, vp, vp, vp, vp],

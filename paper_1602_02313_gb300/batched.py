@@ -11,6 +11,12 @@ The autotuner picks, per crystal shape, the polarization's K-segment length and 
 size (gw_set_tuning) from timed trial calls, and, for the batch, the number of branches: crystals
 go to branches longest-first onto the least-loaded branch (their measured single-crystal times),
 each candidate graph is captured and timed, and the fastest is kept.
+
+The queued schedule (step_queued, capture_queued) runs the batch on one stream instead: for each
+q index, the polarizations of every crystal that has that q go to one persistent launch whose
+blocks pull (crystal, K segment, strip, tau) units from a device counter
+(gw_polarization_many); each crystal's transforms, screening and self-energy of that q follow.
+Its results equal the per-crystal chains' bit for bit.
 """
 from __future__ import annotations
 
@@ -19,7 +25,8 @@ import os
 
 import torch
 
-from . import (GW, GW_CPE, GW_FP16X2, GW_TUNE_POL_PART_MB, GW_TUNE_POL_SEG_CHUNKS)
+from . import (GW, GW_BOSE, GW_CPE, GW_FP16X2, GW_IW_TO_TAU, GW_TAU_TO_IW, GW_TUNE_POL_PART_MB,
+               GW_TUNE_POL_SEG_CHUNKS, polarization_many)
 from .driver import Chain, contraction_flops
 
 
@@ -184,6 +191,43 @@ class Batch:
                 del g
         self.graph, self.nbranch, self.groups = best[2], best[1], best[3]
         return res
+
+    # ------------------------------------------------------------------ device-queue schedule
+    def step_queued(self):
+        """One GW iteration of every crystal on the capture stream, q index by q index: one
+        gw_polarization_many per index over all crystals that have it (at most 16 per call), then
+        per crystal the bosonic transforms, the screening and the self-energy of that q."""
+        with torch.cuda.stream(self.s0):
+            for ctx, ch in zip(self.ctxs, self.chains):
+                ctx.set_stream(self.s0)
+                ch.start_g0()
+                ch.S.zero_()
+                ch.Sx.zero_()
+            for j in range(max(len(ch.iqs) for ch in self.chains)):
+                jobs = [i for i, ch in enumerate(self.chains) if j < len(ch.iqs)]
+                for g0 in range(0, len(jobs), 16):
+                    grp = jobs[g0:g0 + 16]
+                    polarization_many([self.ctxs[i] for i in grp], [self.chains[i].iqs[j] for i in grp],
+                                      [self.chains[i].G for i in grp], [self.chains[i].P[0] for i in grp],
+                                      self.chains[grp[0]].prec)
+                for i in jobs:
+                    ctx, ch = self.ctxs[i], self.chains[i]
+                    iq, ni = ch.iqs[j], ch.ni
+                    ctx.tau_to_freq_many(GW_BOSE, GW_TAU_TO_IW, 1, ni * ni, ch.P, ch.Piv, ch.bose_prec)
+                    ctx.screen(iq, 1, ch.Piv[:1], ch.Wiv[:1], ch.info[:1], ch.screen_prec)
+                    ctx.tau_to_freq_many(GW_BOSE, GW_IW_TO_TAU, 1, ni, ch.Wiv, ch.Wt, ch.bose_prec)
+                    ch._sigma_q(j, iq, ch.G, ch.occ, ch.Wt[0])
+            for ch in self.chains:
+                ch.finish()
+
+    def capture_queued(self):
+        """The queued schedule as one CUDA graph (run step_queued once eagerly first)."""
+        g = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize(self.device)
+        with torch.cuda.graph(g, stream=self.s0):
+            self.step_queued()
+        self.graph_queued = g
+        return g
 
     def replay(self):
         with torch.cuda.stream(self.s0):

@@ -927,6 +927,21 @@ gw_status gw_polarization(gw_ctx* c, int iq, const double* G, gw_prec prec, doub
   return GW_EINVAL;
 }
 
+gw_status gw_polarization_many(int njobs, gw_ctx* const* ctxs, const int* iqs, const double* const* G_tau,
+                               double* const* P_tau, gw_prec prec) {
+  if (njobs < 1 || njobs > 16 || !ctxs || !iqs || !G_tau || !P_tau) return GW_EINVAL;
+  for (int j = 0; j < njobs; ++j) {
+    if (!ctxs[j] || !G_tau[j] || !P_tau[j]) return GW_EINVAL;
+    if (iqs[j] < 0 || iqs[j] >= ctxs[j]->nq) return set_err(ctxs[0], GW_EINVAL, "gw_polarization_many: q index");
+    if (ctxs[j]->device != ctxs[0]->device)
+      return set_err(ctxs[0], GW_EINVAL, "gw_polarization_many: contexts on different devices");
+    for (int i = 0; i < j; ++i)
+      if (ctxs[i] == ctxs[j]) return set_err(ctxs[0], GW_EINVAL, "gw_polarization_many: a context appears twice");
+  }
+  if (prec != GW_FP16X2) return set_err(ctxs[0], GW_EUNSUPPORTED, "gw_polarization_many: only GW_FP16X2");
+  return launch_pol_many(njobs, ctxs, iqs, G_tau, P_tau);
+}
+
 gw_status gw_tau_to_freq_many(gw_ctx* c, gw_stat stat, gw_dir dir, int count, int64_t batch, const double* in,
                               gw_prec prec, double* out) {
   if (!c || !in || !out || batch <= 0 || count <= 0 || count > 65535) return GW_EINVAL;

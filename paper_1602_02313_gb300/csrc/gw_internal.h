@@ -147,6 +147,7 @@ gw_status launch_dyson(gw_ctx* c, const double* eps, const double* sigx, const d
                        const double* sigc_iw, double* G, double* occ);
 gw_status launch_pol_fp64(gw_ctx* c, int iq, const double* G, double* P);
 gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double* P);
+gw_status launch_pol_many(int njobs, gw_ctx* const* ctxs, const int* iqs, const double* const* G, double* const* P);
 gw_status launch_transform(gw_ctx* c, int stat, int dir, int prec, int count, int64_t batch, const double* in,
                            double* out);
 gw_status launch_screen(gw_ctx* c, int iq0, int nqb, int prec, const double* P, double* W, int* info,

@@ -147,42 +147,44 @@ __global__ void k_split_y(const double2* __restrict__ Mq, int nk, int ni, int np
   *reinterpret_cast<h8*>(lo + sw128_off(r, 32 + 8 * g8) / 2) = il;
 }
 
-__global__ void __launch_bounds__(PT_THREADS, 1)
-    k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
-             int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, float* __restrict__ part,
-             int* __restrict__ err, long long wait_cycles, int stall) {
-  extern __shared__ __align__(1024) unsigned char smraw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-  PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int u = blockIdx.x;
-  const int it = u % ntau, strip = (u / ntau) % nstrips, seg = seg0 + u / (ntau * nstrips);
-  const int4 sd = strips[strip];                 // (row block, c0, N, -)
+// One polarization job: the operands of one (context, q) and where its partials go.
+struct PolJob {
+  const __half* YS;
+  const float* wt;
+  float* part;
+  const int4* strips;
+  int nk, ni, ntau, cpk, npw, nstrips, nseg, seg0;
+  int units;  // K segments x strips x tau of this job (this launch's segments)
+};
+
+// Barrier phases of a block that runs several work units one after another: the chunk counter
+// runs on across units (stage = chunk & 1, phase of that stage = chunk >> 1), and the MMA thread
+// commits `done` once per unit.
+struct PolPhase {
+  int cbase = 0;   // chunks of the units already run by this block
+  int units = 0;   // units already run (commits of `done`)
+  int last0 = -1;  // (thread 0) last chunk whose copies went to stage 0 / 1
+  int last1 = -1;
+};
+
+// One work unit u of job J = (K segment, 128 x N strip of the upper triangle, tau): the producer
+// warps build X = w_tau(p) A and bring Y by bulk copy, one thread issues the MMAs, the producer
+// warps then move the FP32 partial strip out of TMEM. A wait that runs out raises S.abort_flag.
+__device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, unsigned char* base, uint32_t tbase,
+                                         int tid, int warp, int lane, PolPhase& ph, int* err, long long wait_cycles,
+                                         int stall) {
+  const int ntau = J.ntau, nstrips = J.nstrips, cpk = J.cpk, npw = J.npw;
+  const int it = u % ntau, strip = (u / ntau) % nstrips, seg = J.seg0 + u / (ntau * nstrips);
+  const int4 sd = J.strips[strip];  // (row block, c0, N, -)
   const int xb = sd.x, c0 = sd.y, N = sd.z;
-  const int nib = (ni + 127) / 128;
-  const int total = nk * cpk;
-  const int L = (total + nseg - 1) / nseg;
+  const int nib = (J.ni + 127) / 128;
+  const int total = J.nk * cpk;
+  const int L = (total + J.nseg - 1) / J.nseg;
   const int g0 = seg * L, g1 = min(total, g0 + L);
   const int nchunk = max(0, g1 - g0);
   const uint32_t ybytes_slice = (uint32_t)N * 128;
-
-  if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&S.full[s], 257);
-      mbar_init(&S.empty[s], 1);
-    }
-    mbar_init(&S.done, 1);
-    mbar_init(&S.never, 1);
-    S.abort_flag = 0;
-    S.abort_prod[0] = S.abort_prod[1] = 0;
-    S.no_dealloc = 0;
-    fence_mbar_init();
-  }
-  if (warp == 8) tmem_alloc(&S.tslot, 512);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = S.tslot;
+  const __half* YS = J.YS;
+  const float* wt = J.wt;
 
   if (warp < 8) {
     // ------------------------------------------------------------ producers
@@ -218,22 +220,21 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       }
     };
     Item cur[2], nxt[2];
-    int last0 = -1, last1 = -1;  // (thread 0) last chunk whose copies went to stage 0 / 1
     if (nchunk > 0) fetch(0, cur);
     for (int i = 0; i < nchunk; ++i) {
-      const int s = i & 1;
-      // All 256 producer threads take the same go / stop decision for chunk i (their flag slot is
-      // written only before this barrier, and slot i & 1 is not written again before every thread
+      const int ic = ph.cbase + i, s = ic & 1;
+      // All 256 producer threads take the same go / stop decision for chunk ic (their flag slot is
+      // written only before this barrier, and slot ic & 1 is not written again before every thread
       // has read it), so every chunk whose copies are issued gets all its arrivals and its full
-      // barrier completes once the bytes land: the drain below can wait for it.
-      if (i >= 2 && !wait_bar(&S.empty[s], ((i >> 1) + 1) & 1, &S.abort_flag, err, wait_cycles)) S.abort_prod[s] = 1;
+      // barrier completes once the bytes land: the drain can wait for it.
+      if (ic >= 2 && !wait_bar(&S.empty[s], ((ic >> 1) + 1) & 1, &S.abort_flag, err, wait_cycles)) S.abort_prod[s] = 1;
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (S.abort_prod[s]) break;
       unsigned char* st = base + s * P_STAGE_BYTES;
       if (tid == 0) {
         // Y: rows [c0, c0 + N) = whole or leading parts of 128-row blocks, hi and lo slices
         const int g = g0 + i, k = g / cpk, c = g % cpk;
-        if (s) last1 = i; else last0 = i;
+        if (s) ph.last1 = ic; else ph.last0 = ic;
         mbar_arrive_expect_tx(&S.full[s], 2 * ybytes_slice);
         for (int r0 = 0; r0 < N; r0 += 128) {
           const int rows = min(128, N - r0);
@@ -265,19 +266,14 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 2; ++j) cur[j] = nxt[j];
     }
-    // bulk copies still in flight into this block's shared memory land before it exits
-    if (tid == 0) {
-      if (last0 >= 0 && !drain_bar(&S.full[0], (last0 >> 1) & 1)) S.no_dealloc = 1;
-      if (last1 >= 0 && !drain_bar(&S.full[1], (last1 >> 1) & 1)) S.no_dealloc = 1;
-    }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
     const uint32_t id = idesc_f16(128, N, false, false), idn = idesc_f16(128, N, false, true);
     const uint32_t dre = tbase, dim = tbase + N;
-    if (stall) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall: runs out
+    if (stall && ph.units == 0) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall
     for (int i = 0; i < nchunk; ++i) {
-      const int s = i & 1;
-      if (S.abort_flag || !wait_bar(&S.full[s], (i >> 1) & 1, &S.abort_flag, err, wait_cycles)) break;
+      const int ic = ph.cbase + i, s = ic & 1;
+      if (S.abort_flag || !wait_bar(&S.full[s], (ic >> 1) & 1, &S.abort_flag, err, wait_cycles)) break;
       tc_fence_after();
       const uint32_t st = smem_u32(base + s * P_STAGE_BYTES);
       const uint32_t xh = st, xl = st + P_XT, yh = st + 2 * P_XT, yl = yh + ybytes_slice;
@@ -298,16 +294,16 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
       mma_commit(&S.empty[s]);
     }
     mma_commit(&S.done);
-    if (!drain_bar(&S.done, 0)) S.no_dealloc = 1;  // every MMA issued here has completed
   }
 
   // ------------------------------------------------------------ epilogue: FP32 partial strips (8 warps)
+  // The next unit's MMAs overwrite TMEM only after these threads have armed its first chunk.
   if (warp < 8) {
-    const bool ok = nchunk > 0 && wait_bar(&S.done, 0, &S.abort_flag, err, wait_cycles) && !S.abort_flag;
+    const bool ok = nchunk > 0 && wait_bar(&S.done, ph.units & 1, &S.abort_flag, err, wait_cycles) && !S.abort_flag;
     tc_fence_after();
     const int quad = warp & 3, half = warp >> 2;
     const int row = 32 * quad + lane;
-    float* out = part + (size_t)u * 2 * 128 * 256;
+    float* out = J.part + (size_t)u * 2 * 128 * 256;
     const int nb16 = N / 16;
     const int ab = 4 * xb + quad;  // the 32-row block of this warp's rows
     for (int acc = 0; acc < 2; ++acc) {
@@ -325,10 +321,103 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
         for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
       }
     }
+    tc_fence_before();
+  }
+  ph.cbase += nchunk;
+  ph.units += 1;
+}
+
+__device__ __forceinline__ void pol_block_init(PolSmem& S, int tid, int warp) {
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&S.full[s], 257);
+      mbar_init(&S.empty[s], 1);
+    }
+    mbar_init(&S.done, 1);
+    mbar_init(&S.never, 1);
+    S.abort_flag = 0;
+    S.abort_prod[0] = S.abort_prod[1] = 0;
+    S.no_dealloc = 0;
+    fence_mbar_init();
+  }
+  if (warp == 8) tmem_alloc(&S.tslot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+}
+
+// The block's last act: the copies still in flight into its shared memory land and its MMAs
+// complete before it frees the tensor memory (if either does not, it keeps it and only reports).
+// Called after a block barrier that follows the last unit's epilogue: every waiter on `done` is
+// past its phase when the MMA thread commits `done` once more here.
+__device__ __forceinline__ void pol_block_finish(PolSmem& S, uint32_t tbase, int tid, int warp, int lane,
+                                                 PolPhase& ph) {
+  if (tid == 0) {
+    if (ph.last0 >= 0 && !drain_bar(&S.full[0], (ph.last0 >> 1) & 1)) S.no_dealloc = 1;
+    if (ph.last1 >= 0 && !drain_bar(&S.full[1], (ph.last1 >> 1) & 1)) S.no_dealloc = 1;
+  }
+  if (warp == 8 && lane == 0) {
+    mma_commit(&S.done);
+    if (!drain_bar(&S.done, ph.units & 1)) S.no_dealloc = 1;  // every MMA issued here has completed
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 8 && !S.no_dealloc) tmem_dealloc(tbase, 512);
+}
+
+// One work unit per block: the units of one (context, q).
+__global__ void __launch_bounds__(PT_THREADS, 1)
+    k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
+             int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, float* __restrict__ part,
+             int* __restrict__ err, long long wait_cycles, int stall) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pol_block_init(S, tid, warp);
+  const uint32_t tbase = S.tslot;
+  PolJob J{YS, wt, part, strips, nk, ni, ntau, cpk, npw, nstrips, nseg, seg0, 0};
+  PolPhase ph;
+  pol_unit(J, blockIdx.x, S, base, tbase, tid, warp, lane, ph, err, wait_cycles, stall);
+  // the epilogue has seen the unit's `done` phase before the MMA thread commits `done` again in
+  // the finish (two commits completing back to back would move the barrier two phases on)
+  __syncthreads();
+  pol_block_finish(S, tbase, tid, warp, lane, ph);
+}
+
+// The batched form: up to kPolQueueJobs (context, q) jobs, their units numbered one after another;
+// one block per SM pulls the next unit from a device counter until all are taken (the blocks that
+// finish early take more), so that small jobs fill the GPU beside large ones in one launch.
+constexpr int kPolQueueJobs = 16;
+struct PolQueue {
+  PolJob job[kPolQueueJobs];
+  int njobs, total;
+};
+
+__global__ void __launch_bounds__(PT_THREADS, 1)
+    k_pol_tc_queue(const __grid_constant__ PolQueue Q, int* __restrict__ counter, int* __restrict__ err,
+                   long long wait_cycles, int stall) {
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+  PolSmem& S = *reinterpret_cast<PolSmem*>(base + 2 * P_STAGE_BYTES);
+  __shared__ int item;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  pol_block_init(S, tid, warp);
+  const uint32_t tbase = S.tslot;
+  PolPhase ph;
+  while (true) {
+    if (tid == 0) item = S.abort_flag ? Q.total : atomicAdd(counter, 1);
+    __syncthreads();
+    const int w = item;
+    __syncthreads();  // every thread has read `item` before thread 0 writes the next one
+    if (w >= Q.total) break;
+    int j = 0, u = w;
+    while (j + 1 < Q.njobs && u >= Q.job[j].units) u -= Q.job[j++].units;
+    pol_unit(Q.job[j], u, S, base, tbase, tid, warp, lane, ph, err, wait_cycles, stall);
+    __syncthreads();            // every role is done with the unit: the abort flag no longer changes
+    if (S.abort_flag) break;    // the same decision in every thread
+  }
+  pol_block_finish(S, tbase, tid, warp, lane, ph);
 }
 
 // h + l += x with the rounding error of h + x kept exactly in l (Knuth's two-sum)
@@ -723,8 +812,19 @@ int num_sms(gw_ctx* c) {
 
 }  // namespace
 
-gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double* P) {
-  if (prec != GW_FP16X2) return set_err(c, GW_EUNSUPPORTED, "polarization: only GW_FP16X2 is built on tensor cores");
+// Host plan of one polarization job: strips, K segments, workspace, and the operand image and
+// pair weights of its q, built on the context's stream.
+struct PolPrep {
+  int nstrips = 0, nseg = 0, seg_pass = 0, base_units = 0, nb32 = 0, cpk = 0, npw = 0;
+  float* d_part = nullptr;
+  float* d_wt = nullptr;
+  __half* d_ys = nullptr;
+  int4* d_strips = nullptr;
+  int* d_strip_of = nullptr;
+  double scale = 0.0;
+};
+
+static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   const int ni = c->ni, nib = (ni + 127) / 128, nb32 = (ni + 31) / 32;
   // strips covering the upper triangle: rows of block i, columns [128 i, ni) in pieces <= 256
   std::vector<int4> strips;
@@ -783,23 +883,99 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
   k_pol_weights<<<(unsigned)((nwt + 255) / 256), 256, 0, c->stream>>>(G, c->d_kmq + (size_t)iq * c->nk, c->nk, c->nb,
                                                                       c->ntau, npw, d_wt);
   if ((st = check_launch(c, "pol_weights")) != GW_OK) return st;
-  const size_t smem = 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem);
+  pp->nstrips = nstrips;
+  pp->nseg = nseg;
+  pp->seg_pass = seg_pass;
+  pp->base_units = base_units;
+  pp->nb32 = nb32;
+  pp->cpk = cpk;
+  pp->npw = npw;
+  pp->d_part = d_part;
+  pp->d_wt = d_wt;
+  pp->d_ys = d_ys;
+  pp->d_strips = d_strips;
+  pp->d_strip_of = d_strip_of;
+  pp->scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
+  return GW_OK;
+}
+
+// Sum the partials of the segments [s0, s0 + ns) into P (the first pass writes, later ones add).
+static gw_status pol_reduce(gw_ctx* c, const PolPrep& pp, int s0, int ns, double* P) {
+  k_pol_reduce<<<dim3(pp.nb32 * (pp.nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(
+      pp.d_part, c->ni, c->ntau, pp.d_strip_of, pp.nstrips, pp.d_strips, ns, pp.scale, s0 > 0 ? 1 : 0, (double2*)P);
+  return check_launch(c, "pol_reduce");
+}
+
+static size_t pol_smem() { return 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem); }
+
+gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double* P) {
+  if (prec != GW_FP16X2) return set_err(c, GW_EUNSUPPORTED, "polarization: only GW_FP16X2 is built on tensor cores");
+  PolPrep pp;
+  gw_status st;
+  if ((st = pol_prepare(c, iq, G, &pp)) != GW_OK) return st;
+  const size_t smem = pol_smem();
   cudaFuncSetAttribute(k_pol_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const double scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
-  for (int s0 = 0; s0 < nseg; s0 += seg_pass) {
-    const int ns = std::min(seg_pass, nseg - s0);
+  for (int s0 = 0; s0 < pp.nseg; s0 += pp.seg_pass) {
+    const int ns = std::min(pp.seg_pass, pp.nseg - s0);
     kt_begin(c, "k_pol_tc");
-    k_pol_tc<<<base_units * ns, PT_THREADS, smem, c->stream>>>(d_ys, d_wt, c->nk, ni, c->ntau, cpk, npw, nstrips,
-                                                               d_strips, nseg, s0, d_part, c->d_err, c->wait_cycles,
-                                                               c->fault_stall);
+    k_pol_tc<<<pp.base_units * ns, PT_THREADS, smem, c->stream>>>(pp.d_ys, pp.d_wt, c->nk, c->ni, c->ntau, pp.cpk,
+                                                                  pp.npw, pp.nstrips, pp.d_strips, pp.nseg, s0,
+                                                                  pp.d_part, c->d_err, c->wait_cycles, c->fault_stall);
     kt_end(c);
     if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
-    k_pol_reduce<<<dim3(nb32 * (nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(d_part, ni, c->ntau, d_strip_of, nstrips,
-                                                                             d_strips, ns, scale, s0 > 0 ? 1 : 0,
-                                                                             (double2*)P);
-    if ((st = check_launch(c, "pol_reduce")) != GW_OK) return st;
+    if ((st = pol_reduce(c, pp, s0, ns, P)) != GW_OK) return st;
   }
   return GW_OK;
+}
+
+// Several (context, q) polarizations in one persistent launch per pass over K segments, on the
+// first context's stream: each job's operand image and weights are built on that stream, then
+// one block per SM pulls (job, K segment, strip, tau) units from a device counter.
+gw_status launch_pol_many(int njobs, gw_ctx* const* ctxs, const int* iqs, const double* const* G, double* const* P) {
+  gw_ctx* c0 = ctxs[0];
+  std::vector<PolPrep> pp(njobs);
+  std::vector<cudaStream_t> saved(njobs);
+  gw_status st = GW_OK;
+  for (int j = 0; j < njobs; ++j) {
+    saved[j] = ctxs[j]->stream;
+    ctxs[j]->stream = c0->stream;
+  }
+  for (int j = 0; j < njobs && st == GW_OK; ++j) st = pol_prepare(ctxs[j], iqs[j], G[j], &pp[j]);
+  std::vector<int> s0(njobs, 0);
+  const size_t smem = pol_smem();
+  cudaFuncSetAttribute(k_pol_tc_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int* counter = c0->d_err + 1;
+  while (st == GW_OK) {
+    PolQueue Q{};
+    Q.njobs = 0;
+    Q.total = 0;
+    std::vector<int> jid, nsj;
+    for (int j = 0; j < njobs; ++j) {
+      if (s0[j] >= pp[j].nseg) continue;
+      const int ns = std::min(pp[j].seg_pass, pp[j].nseg - s0[j]);
+      gw_ctx* c = ctxs[j];
+      PolJob& J = Q.job[Q.njobs++];
+      J = PolJob{pp[j].d_ys, pp[j].d_wt, pp[j].d_part, pp[j].d_strips, c->nk, c->ni, c->ntau, pp[j].cpk,
+                 pp[j].npw, pp[j].nstrips, pp[j].nseg, s0[j], pp[j].base_units * ns};
+      Q.total += J.units;
+      jid.push_back(j);
+      nsj.push_back(ns);
+    }
+    if (Q.njobs == 0) break;
+    cudaMemsetAsync(counter, 0, sizeof(int), c0->stream);
+    kt_begin(c0, "k_pol_tc");
+    k_pol_tc_queue<<<num_sms(c0), PT_THREADS, smem, c0->stream>>>(Q, counter, c0->d_err, c0->wait_cycles,
+                                                                  c0->fault_stall);
+    kt_end(c0);
+    if ((st = check_launch(c0, "pol_tc_queue")) != GW_OK) break;
+    for (size_t q = 0; q < jid.size() && st == GW_OK; ++q) {
+      const int j = jid[q];
+      st = pol_reduce(ctxs[j], pp[j], s0[j], nsj[q], P[j]);
+      s0[j] += nsj[q];
+    }
+  }
+  for (int j = 0; j < njobs; ++j) ctxs[j]->stream = saved[j];
+  return st;
 }
 
 gw_status launch_sigma_mixed(gw_ctx* c, int iq, const double* G, const double* W, int prec, double* S) {

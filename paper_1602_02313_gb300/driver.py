@@ -178,18 +178,28 @@ class Chain:
         self.sigma()
         self.finish()
         self.vxc = self.Sx.clone()  # Sigma_0 = Sigma^x[G0], kept fixed by the later passes
+        self.G_in = None
 
-    def iterate(self, n, gw0=False):
+    def iterate(self, n, gw0=False, mix=1.0):
         """n self-consistent passes after step(): P, W~ and Sigma from the previous pass's
         dressed G (Eqs. dysongf-zcjk solved in i w), the Dyson update from the band energies
         with the new Sigma and the fixed reference potential. gw0=True keeps W~ of the first
-        pass (the chain must be built with keep_w=True) and updates only G and Sigma."""
+        pass (the chain must be built with keep_w=True) and updates only G and Sigma.
+        mix < 1 feeds each pass the linear mixture G_in = mix G_out + (1 - mix) G_in(previous)
+        of the dressed G and of its occupations (the first pass's G_in(previous) is G0); the
+        paper's passes are mix = 1."""
         if self.vxc is None:
             raise GwError("Chain.iterate: run step() first")
         if gw0 and self.Wkeep is None:
             raise GwError("Chain.iterate: GW0 needs a chain built with keep_w=True")
+        if not hasattr(self, "G_in") or self.G_in is None:
+            self.G_in, self.occ_in = self.G.clone(), self.occ.clone()
         for _ in range(n):
-            G, occ = self.G1.clone(), self.occ1.clone()
+            if mix == 1.0:
+                G, occ = self.G1.clone(), self.occ1.clone()
+            else:
+                G = self.G_in.mul_(1.0 - mix).add_(self.G1, alpha=mix).clone()
+                occ = self.occ_in.mul_(1.0 - mix).add_(self.occ1, alpha=mix).clone()
             if gw0:
                 self.sigma_fixed_w(G, occ)
             else:

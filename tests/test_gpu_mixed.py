@@ -97,8 +97,9 @@ def test_selfenergy_tc(gw, name, case):
 
 
 def test_c2_full_size_tc_vs_fp64(gw):
-    """Bench sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48): tensor-core P and Sigma of
-    one q against the FP64 GPU path (itself pinned to the oracle in test_gpu_parity)."""
+    """Bench sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48), in the bench's launch configuration:
+    tensor-core P and Sigma of one q against the FP64 GPU path everywhere, and against the oracle
+    at sampled tau (P) and sampled (k, tau) (Sigma^c)."""
     cr, gr = gi.make_config("nk64_nb64", qlist=[7])
     ctx = gw.GW(gr, cr)
     G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
@@ -126,6 +127,18 @@ def test_c2_full_size_tc_vs_fp64(gw):
     print(f"Nk=64: Sigma tensor-core vs FP64 rel err {e:.3e}; Sigma^x float-float vs FP64 {ex:.3e}")
     assert e < TOL_S
     assert ex < TOL_SX_FF
+    # against the oracle at sampled points
+    its, ks = [0, 24, 47], [0, 63]
+    M = gi.m_for_q(cr, 0)
+    Pr = orc.polarization(M, G, cr.kmq[0], its=its)
+    eP = rel(host(P16)[its], Pr)
+    Wh = host(W)
+    Sr, Sxr, _ = orc.selfenergy(M[ks], G, Wh, cr.v[0], cr.kmq[0], occ, ks=ks, its=its)
+    S16h, Sx16h = host(S16), host(Sx16)
+    eS = max(rel(S16h[k][:, its], Sr[k][:, its]) for k in ks)
+    eX = max(rel(Sx16h[k], Sxr[k]) for k in ks)
+    print(f"Nk=64 vs oracle: P tensor-core {eP:.3e}, Sigma^c tensor-core {eS:.3e}, Sigma^x float-float {eX:.3e}")
+    assert eP < TOL_P and eS < TOL_S and eX < TOL_SX_FF
 
 
 def test_chain_qp_gap_mixed_vs_fp64(gw):
@@ -135,9 +148,10 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
     from paper_1602_02313_gb300.driver import Chain
     cr, gr = gi.make_config("nk64_nb64", nk=8)
     res = {}
-    # the mixed chain as the bench runs it (FP32 dielectric solve), and with the float-float solve
+    # the mixed chain as the bench runs it (float-float dielectric solve, the default), and with the
+    # plain FP32 solve
     runs = [("fp64", gw.GW_FP64, None, (gw.GW_PADE, gw.GW_CPE)), ("fp16x2", gw.GW_FP16X2, None, (gw.GW_PADE, gw.GW_CPE)),
-            ("fp16x2_ffscreen", gw.GW_FP16X2, gw.GW_F32X2, (gw.GW_CPE,))]
+            ("fp16x2_f32screen", gw.GW_FP16X2, gw.GW_F32, (gw.GW_CPE,))]
     for name, prec, sprec, conts in runs:
         for cont in conts:
             ctx = gw.GW(gr, cr, omega=gi.OMEGA_SI)
@@ -160,10 +174,10 @@ def test_chain_qp_gap_mixed_vs_fp64(gw):
         assert eS < 1e-3
     a, b = res[("fp64", gw.GW_CPE)], res[("fp16x2", gw.GW_CPE)]
     assert abs(gap(a["eqp"]) - gap(b["eqp"])) * ha2mev < 1.0  # the 1 meV target, CPE continuation
-    # the same with the dielectric solve in float-float instead of FP32
-    c = res[("fp16x2_ffscreen", gw.GW_CPE)]
+    # the same with the dielectric solve in plain FP32 instead of float-float
+    c = res[("fp16x2_f32screen", gw.GW_CPE)]
     dE, dgap = np.abs(a["eqp"] - c["eqp"]).max(), abs(gap(a["eqp"]) - gap(c["eqp"]))
-    print(f"chain nk=8 cpe, float-float screening: Sigma^c rel err {rel(c['S'], a['S']):.3e}; max |dE_qp| "
+    print(f"chain nk=8 cpe, FP32 screening: Sigma^c rel err {rel(c['S'], a['S']):.3e}; max |dE_qp| "
           f"{dE * ha2mev:.4f} meV; |dgap| {dgap * ha2mev:.4f} meV")
     assert rel(c["S"], a["S"]) < 1e-3
     assert dgap * ha2mev < 1.0
@@ -207,3 +221,28 @@ def test_ni512_shapes_tc_vs_fp64(gw):
     e = rel(host(S16), host(S64))
     print(f"NI=512: Sigma tensor-core vs FP64 rel err {e:.3e}")
     assert e < TOL_S
+
+
+def test_c3_full_size_sigma_tc_sampled(gw):
+    """The Nk=216 crystal at its full size (Nk = 216, Nb = 128, NI = 512, Ntau = 64; M generated per q
+    on demand, as the bench's c3 run does), one q: the tensor-core Sigma^c (output columns in two
+    parts) and the float-float Sigma^x against the oracle at sampled k and tau, with a Hermitian
+    stand-in for W~(tau)."""
+    cr, gr = gi.make_config("nk216_nb128", qlist=[7])
+    ctx = gw.GW(gr, cr, m_mode=2)
+    G, occ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((gr.ntau, cr.ni, 8)) + 1j * rng.standard_normal((gr.ntau, cr.ni, 8))
+    W = -30.0 * (X @ np.conj(np.swapaxes(X, 1, 2))) / 8
+    S = zeros((cr.nk, cr.nb, gr.ntau))
+    Sx = zeros((cr.nk, cr.nb))
+    ctx.selfenergy(0, dev(G), dev(occ), dev(W), S, Sx, gw.GW_FP16X2)
+    ctx.sync()
+    ks, its = [0, 101, 215], [0, 37, 63]
+    Sr, Sxr, _ = orc.selfenergy(gi.m_for_q(cr, 0, ks=ks), G, W, cr.v[0], cr.kmq[0], occ, ks=ks, its=its)
+    Sh, Sxh = host(S), host(Sx)
+    eS = max(rel(Sh[k][:, its], Sr[k][:, its]) for k in ks)
+    eX = max(rel(Sxh[k], Sxr[k]) for k in ks)
+    print(f"Nk=216 vs oracle: Sigma^c tensor-core {eS:.3e}, Sigma^x float-float {eX:.3e}")
+    assert eS < TOL_S and eX < TOL_SX_FF
+    ctx.close()
