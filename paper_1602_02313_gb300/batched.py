@@ -41,9 +41,10 @@ class Batch:
         self.systems = list(systems)
         self.device = device
         self.s0 = torch.cuda.Stream(device)
-        self.ctxs, self.chains = [], []
+        self.ctxs, self.chains, self.cstreams = [], [], []
         for cr, gr in self.systems:
             s = torch.cuda.Stream(device)
+            self.cstreams.append(s)
             ctx = GW(gr, cr, omega=omega, device=device, stream=s, m_mode=1)
             eps = torch.from_numpy(cr.eps).to(f"cuda:{device}")
             self.ctxs.append(ctx)
@@ -194,29 +195,50 @@ class Batch:
 
     # ------------------------------------------------------------------ device-queue schedule
     def step_queued(self):
-        """One GW iteration of every crystal on the capture stream, q index by q index: one
-        gw_polarization_many per index over all crystals that have it (at most 16 per call), then
-        per crystal the bosonic transforms, the screening and the self-energy of that q."""
-        with torch.cuda.stream(self.s0):
+        """One GW iteration of every crystal, the q indices in blocks of the chains' q-block size:
+        on the capture stream, per q index one gw_polarization_many over all crystals that have it
+        (at most 16 per call); then each crystal's bosonic transforms and screening of the block's
+        q points and their self-energies on the crystal's own stream (forked from and joined back
+        to the capture stream by events, so that the crystals' post-polarization work overlaps and
+        the next block's polarizations wait for it)."""
+        s0 = self.s0
+        qb = min(ch.qb for ch in self.chains)
+        with torch.cuda.stream(s0):
             for ctx, ch in zip(self.ctxs, self.chains):
-                ctx.set_stream(self.s0)
+                ctx.set_stream(s0)
                 ch.start_g0()
                 ch.S.zero_()
                 ch.Sx.zero_()
-            for j in range(max(len(ch.iqs) for ch in self.chains)):
-                jobs = [i for i, ch in enumerate(self.chains) if j < len(ch.iqs)]
-                for g0 in range(0, len(jobs), 16):
-                    grp = jobs[g0:g0 + 16]
-                    polarization_many([self.ctxs[i] for i in grp], [self.chains[i].iqs[j] for i in grp],
-                                      [self.chains[i].G for i in grp], [self.chains[i].P[0] for i in grp],
-                                      self.chains[grp[0]].prec)
-                for i in jobs:
-                    ctx, ch = self.ctxs[i], self.chains[i]
-                    iq, ni = ch.iqs[j], ch.ni
-                    ctx.tau_to_freq_many(GW_BOSE, GW_TAU_TO_IW, 1, ni * ni, ch.P, ch.Piv, ch.bose_prec)
-                    ctx.screen(iq, 1, ch.Piv[:1], ch.Wiv[:1], ch.info[:1], ch.screen_prec)
-                    ctx.tau_to_freq_many(GW_BOSE, GW_IW_TO_TAU, 1, ni, ch.Wiv, ch.Wt, ch.bose_prec)
-                    ch._sigma_q(j, iq, ch.G, ch.occ, ch.Wt[0])
+            for j0 in range(0, max(len(ch.iqs) for ch in self.chains), qb):
+                for j in range(j0, j0 + qb):
+                    jobs = [i for i, ch in enumerate(self.chains) if j < len(ch.iqs)]
+                    for g0 in range(0, len(jobs), 16):
+                        grp = jobs[g0:g0 + 16]
+                        polarization_many([self.ctxs[i] for i in grp], [self.chains[i].iqs[j] for i in grp],
+                                          [self.chains[i].G for i in grp],
+                                          [self.chains[i].P[j - j0] for i in grp], self.chains[grp[0]].prec)
+                fork = torch.cuda.Event()
+                fork.record(s0)
+                joins = []
+                for ctx, ch, st in zip(self.ctxs, self.chains, self.cstreams):
+                    js = list(range(j0, min(j0 + qb, len(ch.iqs))))
+                    if not js:
+                        continue
+                    st.wait_event(fork)
+                    ctx.set_stream(st)
+                    with torch.cuda.stream(st):
+                        nb_, ni = len(js), ch.ni
+                        ctx.tau_to_freq_many(GW_BOSE, GW_TAU_TO_IW, nb_, ni * ni, ch.P, ch.Piv, ch.bose_prec)
+                        ctx.screen(ch.iqs[j0], nb_, ch.Piv[:nb_], ch.Wiv[:nb_], ch.info[:nb_], ch.screen_prec)
+                        ctx.tau_to_freq_many(GW_BOSE, GW_IW_TO_TAU, nb_, ni, ch.Wiv, ch.Wt, ch.bose_prec)
+                        for jj, j in enumerate(js):
+                            ch._sigma_q(j, ch.iqs[j], ch.G, ch.occ, ch.Wt[jj])
+                        ev = torch.cuda.Event()
+                        ev.record(st)
+                        joins.append(ev)
+                    ctx.set_stream(s0)
+                for ev in joins:
+                    s0.wait_event(ev)
             for ch in self.chains:
                 ch.finish()
 
