@@ -933,7 +933,8 @@ def main():
     # Hermitian half (NI^2 / 2) with sum_i 128 (NI - 128 i) outputs; Sigma runs 4 real GEMMs over
     # the upper triangle of W~, (nkc + 1) / (2 nkc) of the columns, against 4 NI^2 MACs counted
     ni_ = cr.ni
-    strip_cover = sum(128 * (ni_ - 128 * i) for i in range((ni_ + 127) // 128)) / (ni_ * ni_ / 2.0)
+    # P: E = Re P + Im P in strips of 128 rows over all NI columns (rows padded to 128)
+    strip_cover = 128 * ((ni_ + 127) // 128) / float(ni_)
     nkc_ = ni_ // 32
     mma_factor = {"k_pol_tc": 3.0 * strip_cover, "k_sig_tc": 3.0 * (nkc_ + 1) / (2.0 * nkc_)}
     peaks = _peaks()

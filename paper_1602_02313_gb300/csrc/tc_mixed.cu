@@ -8,11 +8,13 @@
 //
 // polarization, Eq. (irpol), one q, all tau:
 //   P_II'(tau) = pref sum_{k,p} w_p(tau) A_k[I,p] conj(A_k[I',p]),  w_p = -G_b(k|tau) G_a(k-q|beta-tau)
-//   Re P = X Y^T, Im P = X' Y^T with rows X_I = [w Re A_I | w Im A_I], Y_I' = [Re A_I' | Im A_I'],
-//   X'_I = [w Im A_I | -w Re A_I] (same shared-memory tile, other K halves, negated).
-//   Work unit = (K segment, 128-row strip of <= 256 columns of the upper triangle, tau); the
-//   FP32 partial strips are summed over K segments with float-float accumulators by a second
-//   kernel, which also writes the Hermitian lower triangle.
+//   P(tau) is Hermitian (w is real), so the real matrix E = Re P + Im P holds all of it:
+//   Re P = (E + E^T) / 2, Im P = (E - E^T) / 2. E is one real GEMM, E = X Y^T with rows
+//   X_I = [w (Re A_I + Im A_I) | w (Im A_I - Re A_I)], Y_I' = [Re A_I' | Im A_I']: tiles of E
+//   cover NI^2 exactly (the Hermitian half in strips of 128 rows would cover 1.5x of it).
+//   Work unit = (K segment, 128-row strip of <= 256 columns of E, tau); the FP32 partial strips
+//   are summed over K segments with float-float accumulators into E (FP64) by a second kernel,
+//   and a third forms Re P and Im P.
 //
 // self-energy, Eq. (sigc), one q:
 //   d_p(tau) = a_p^H W~(tau) a_p = Re a_p^T Wr Re a_p + Im a_p^T Wr Im a_p + 2 Im a_p^T Wi Re a_p
@@ -80,17 +82,18 @@ struct alignas(16) h8 {
 };
 
 // --------------------------------------------------------------------------- polarization
-// The upper triangle of P is covered by "strips": rows [128 i, 128 i + 128) x columns
-// [c0, c0 + N), c0 >= 128 i, N <= 256. A work unit is (K segment, strip, tau). The unscaled
+// E is covered by "strips": rows [128 i, 128 i + 128) x columns [c0, c0 + N), c0 = 0, 256, ...,
+// N <= 256. A work unit is (K segment, strip, tau). The unscaled
 // operand Y (rows of the strip's columns) is bulk-copied from YS, a pre-split,
 // pre-swizzled image of M[q]:
 //   YS[k][chunk][iblk][slice][128 rows x 128 B], row = [Re A (32 pairs) | Im A (32 pairs)],
-// slices hi, lo. The scaled operand X = w_tau(p) A (rows of the strip) is built by the
-// producer warps from the same image. TMEM holds Re P (N columns) and Im P (N columns).
+// slices hi, lo. The scaled operand X (rows of the strip) is built by the producer warps from the
+// same image. TMEM holds E (N columns).
 constexpr int kPolChunksPerSeg = 32;  // upper bound of the context's K chunks per segment
 constexpr int PT_THREADS = 288;                     // warps 0-7 produce / run the epilogue, warp 8 issues MMAs
 constexpr int P_XT = 16384;                         // one X slice: 128 rows x 128 B
 constexpr int P_STAGE_BYTES = 2 * P_XT + 2 * 256 * 128;  // X hi, lo (128 rows) + Y hi, lo (<= 256 rows)
+constexpr int P_TILE = 128 * 256;                   // floats of one unit's partial strip
 
 struct PolSmem {
   uint64_t full[2], empty[2], done, never;  // never: nothing arrives on it (stall injection)
@@ -167,8 +170,8 @@ struct PolPhase {
   int last1 = -1;
 };
 
-// One work unit u of job J = (K segment, 128 x N strip of the upper triangle, tau): the producer
-// warps build X = w_tau(p) A and bring Y by bulk copy, one thread issues the MMAs, the producer
+// One work unit u of job J = (K segment, 128 x N strip of E, tau): the producer warps build
+// X = [w (Re A + Im A) | w (Im A - Re A)] and bring Y by bulk copy, one thread issues the MMAs, the producer
 // warps then move the FP32 partial strip out of TMEM. A wait that runs out raises S.abort_flag.
 __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, unsigned char* base, uint32_t tbase,
                                          int tid, int warp, int lane, PolPhase& ph, int* err, long long wait_cycles,
@@ -188,7 +191,7 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
 
   if (warp < 8) {
     // ------------------------------------------------------------ producers
-    // X = w A for the strip's 128 rows: 512 items of (row, 8 pairs), two per thread. Within a
+    // X for the strip's 128 rows: 512 items of (row, 8 pairs), two per thread. Within a
     // warp, the 8 lanes of each quarter take rows r and r + 4 (r < 4 of an 8-row group), so
     // their 16-byte stores land in 8 distinct bank groups of the 128-byte swizzle. The next
     // chunk's operands and weights are loaded while the current chunk is written.
@@ -253,8 +256,10 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
         h8 orh, orl, oih, oil;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          split2(wv[e] * (__half2float(cur[j].rh.v[e]) + __half2float(cur[j].rl.v[e])), orh.v[e], orl.v[e]);
-          split2(wv[e] * (__half2float(cur[j].ih.v[e]) + __half2float(cur[j].il.v[e])), oih.v[e], oil.v[e]);
+          const float re = __half2float(cur[j].rh.v[e]) + __half2float(cur[j].rl.v[e]);
+          const float im = __half2float(cur[j].ih.v[e]) + __half2float(cur[j].il.v[e]);
+          split2(wv[e] * (re + im), orh.v[e], orl.v[e]);
+          split2(wv[e] * (im - re), oih.v[e], oil.v[e]);
         }
         *reinterpret_cast<h8*>(st + oRe) = orh;
         *reinterpret_cast<h8*>(st + oIm) = oih;
@@ -268,8 +273,7 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_f16(128, N, false, false), idn = idesc_f16(128, N, false, true);
-    const uint32_t dre = tbase, dim = tbase + N;
+    const uint32_t id = idesc_f16(128, N, false, false);
     if (stall && ph.units == 0) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall
     for (int i = 0; i < nchunk; ++i) {
       const int ic = ph.cbase + i, s = ic & 1;
@@ -281,45 +285,35 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
       for (int ks = 0; ks < 4; ++ks) {
         const uint32_t acc = (i > 0 || ks > 0) ? 1u : 0u;
         const uint32_t bo = 32 * ks;
-        mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yh + bo), id, acc);
-        mma_f16(dre, sdesc_sw128(xh + bo), sdesc_sw128(yl + bo), id, 1);
-        mma_f16(dre, sdesc_sw128(xl + bo), sdesc_sw128(yh + bo), id, 1);
-        // Im P = [w Im A | -w Re A] . [Re A | Im A]: other K half of X, negated for the second half
-        const uint32_t ao = 32 * ((ks + 2) & 3);
-        const uint32_t idx = ks < 2 ? id : idn;
-        mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yh + bo), idx, acc);
-        mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yl + bo), idx, 1);
-        mma_f16(dim, sdesc_sw128(xl + ao), sdesc_sw128(yh + bo), idx, 1);
+        mma_f16(tbase, sdesc_sw128(xh + bo), sdesc_sw128(yh + bo), id, acc);
+        mma_f16(tbase, sdesc_sw128(xh + bo), sdesc_sw128(yl + bo), id, 1);
+        mma_f16(tbase, sdesc_sw128(xl + bo), sdesc_sw128(yh + bo), id, 1);
       }
       mma_commit(&S.empty[s]);
     }
     mma_commit(&S.done);
   }
 
-  // ------------------------------------------------------------ epilogue: FP32 partial strips (8 warps)
+  // ------------------------------------------------------------ epilogue: FP32 partial strip (8 warps)
   // The next unit's MMAs overwrite TMEM only after these threads have armed its first chunk.
   if (warp < 8) {
     const bool ok = nchunk > 0 && wait_bar(&S.done, ph.units & 1, &S.abort_flag, err, wait_cycles) && !S.abort_flag;
     tc_fence_after();
     const int quad = warp & 3, half = warp >> 2;
     const int row = 32 * quad + lane;
-    float* out = J.part + (size_t)u * 2 * 128 * 256;
+    float* out = J.part + (size_t)u * P_TILE + (size_t)row * 256;
     const int nb16 = N / 16;
-    const int ab = 4 * xb + quad;  // the 32-row block of this warp's rows
-    for (int acc = 0; acc < 2; ++acc) {
-      for (int bk = half; bk < nb16; bk += 2) {
-        if (((c0 + 16 * bk) >> 5) < ab) continue;  // below the diagonal: never read back
-        float v[16];
-        if (ok) {
-          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + acc * N + 16 * bk, v);
-        } else {
+    for (int bk = half; bk < nb16; bk += 2) {
+      float v[16];
+      if (ok) {
+        tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + 16 * bk, v);
+      } else {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = 0.f;
-        }
-        float4* o = reinterpret_cast<float4*>(out + ((size_t)acc * 128 + row) * 256 + 16 * bk);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        for (int e = 0; e < 16; ++e) v[e] = 0.f;
       }
+      float4* o = reinterpret_cast<float4*>(out + 16 * bk);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
     tc_fence_before();
   }
@@ -428,64 +422,69 @@ __device__ __forceinline__ void two_sum_acc(float& h, float& l, float x) {
   h = s;
 }
 
-// Sum the FP32 partial strips over K segments and write the Hermitian P (FP64).
-// One block per (32 x 32 block (ab, bb) with ab <= bb, tau); reads are coalesced along
-// the column, the mirrored lower triangle is written through a shared-memory transpose.
-__global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ part, int ni, int ntau,
-                                                    const int* __restrict__ strip_of, int nstrips,
-                                                    const int4* __restrict__ strips, int nseg, double scale,
-                                                    int accumulate, double2* __restrict__ P) {
-  __shared__ double2 tr[32][33];
-  const int nb32 = (ni + 31) / 32;
-  int t = blockIdx.x, ab = 0;
-  while (t >= nb32 - ab) {
-    t -= nb32 - ab;
-    ++ab;
-  }
-  const int bb = ab + t;
-  const int it = blockIdx.y;
-  const int strip = strip_of[ab * nb32 + bb];
-  const int4 sd = strips[strip];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int b = bb * 32 + tx;
-  // float-float accumulators (hi + lo, error-free two-sum per addition): as exact as an FP64
-  // sum of these FP32 terms to ~2^-44, on the FP32 pipes (GB300's FP64 rate is ~1/64 of FP32)
-  float reh[4] = {0, 0, 0, 0}, rel[4] = {0, 0, 0, 0}, imh[4] = {0, 0, 0, 0}, iml[4] = {0, 0, 0, 0};
-  size_t o[4];
+// Sum the FP32 partial strips of E over K segments into E (FP64), one block per (strip, 16-row
+// band, tau): per segment the block reads the band's 16 KB contiguously (float4 per thread), and
+// keeps float-float accumulators (hi + lo, error-free two-sum per addition: as exact as an FP64
+// sum of these FP32 terms to ~2^-44, on the FP32 pipes; GB300's FP64 rate is ~1/64 of FP32).
+__global__ void __launch_bounds__(256, 2) k_pol_sum_e(const float* __restrict__ part, int ni, int ntau, int nstrips,
+                                                      const int4* __restrict__ strips, int nseg,
+                                                      double* __restrict__ E) {
+  const int strip = blockIdx.x >> 3, band = blockIdx.x & 7, it = blockIdx.y;
+  const int4 sd = strips[strip];  // (row block, c0, N, -)
+  const size_t ustride = (size_t)nstrips * ntau * P_TILE;  // one K segment further
+  const float4* p = reinterpret_cast<const float4*>(part + ((size_t)strip * ntau + it) * P_TILE +
+                                                    (size_t)band * 16 * 256) + threadIdx.x;
+  float h[16], l[16];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) o[r] = (size_t)((ab * 32 + ty + 8 * r) & 127) * 256 + (b - sd.y);
-  const size_t ustride = (size_t)nstrips * ntau * 2 * 128 * 256;  // one K segment further
-  const float* pre = part + ((size_t)strip * ntau + it) * 2 * 128 * 256;
+  for (int e = 0; e < 16; ++e) h[e] = l[e] = 0.f;
 #pragma unroll 2
-  for (int s = 0; s < nseg; ++s, pre += ustride) {
-    const float* pim = pre + 128 * 256;
+  for (int sg = 0; sg < nseg; ++sg, p += ustride / 4) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      two_sum_acc(reh[r], rel[r], pre[o[r]]);
-      two_sum_acc(imh[r], iml[r], pim[o[r]]);
+    for (int j = 0; j < 4; ++j) {
+      const float4 v = p[256 * j];
+      two_sum_acc(h[4 * j], l[4 * j], v.x);
+      two_sum_acc(h[4 * j + 1], l[4 * j + 1], v.y);
+      two_sum_acc(h[4 * j + 2], l[4 * j + 2], v.z);
+      two_sum_acc(h[4 * j + 3], l[4 * j + 3], v.w);
     }
   }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int f = threadIdx.x + 256 * j;  // float4 of the band: row f / 64, columns 4 (f % 64) + e
+    const int row = 128 * sd.x + 16 * band + (f >> 6), cl = 4 * (f & 63);
+    if (row < ni && cl < sd.z) {
+      double* o = E + ((size_t)it * ni + row) * ni + sd.y + cl;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = (double)h[4 * j + e] + (double)l[4 * j + e];
+    }
+  }
+}
+
+// P_ab = scale ((E_ab + E_ba) / 2 + i (E_ab - E_ba) / 2), Im P_aa = 0 exactly; one block per
+// (32 x 32 block, tau), E_ba through a shared-memory transpose. accumulate: add to P (a later pass
+// over K segments).
+__global__ void __launch_bounds__(256) k_pol_form(const double* __restrict__ E, int ni, double scale, int accumulate,
+                                                  double2* __restrict__ P) {
+  __shared__ double tb[32][33];
+  const int bx = blockIdx.x, by = blockIdx.y, it = blockIdx.z;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const double* Et = E + (size_t)it * ni * ni;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) tb[ty + 8 * r][tx] = Et[(size_t)(bx * 32 + ty + 8 * r) * ni + by * 32 + tx];
+  __syncthreads();
   double2* Pt = P + (size_t)it * ni * ni;
+  const int b = bx * 32 + tx;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    const int a = ab * 32 + ty + 8 * r;
-    double2 v = make_double2(((double)reh[r] + (double)rel[r]) * scale, ((double)imh[r] + (double)iml[r]) * scale);
-    if (a == b) v.y = 0.0;  // Im P_II = 0 exactly (the tensor-core sum leaves O(2^-22) residue)
-    if (accumulate && a < ni && b < ni) {  // a later pass over K segments: add to the earlier sum
+    const int a = by * 32 + ty + 8 * r;
+    const double e1 = Et[(size_t)a * ni + b], e2 = tb[tx][ty + 8 * r];  // E[a][b], E[b][a]
+    double2 v = make_double2(0.5 * (e1 + e2) * scale, a == b ? 0.0 : 0.5 * (e1 - e2) * scale);
+    if (accumulate) {
       const double2 o = Pt[(size_t)a * ni + b];
       v.x += o.x;
       v.y += o.y;
     }
-    if (a < ni && b < ni && (ab < bb || a <= b)) Pt[(size_t)a * ni + b] = v;
-    tr[ty + 8 * r][tx] = make_double2(v.x, -v.y);
-  }
-  __syncthreads();
-  // lower triangle: P[b'][a'] = conj(P[a'][b']) for a' < b'
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int row = bb * 32 + ty + 8 * r;  // b'
-    const int col = ab * 32 + tx;          // a'
-    if (row < ni && col < ni && col < row) Pt[(size_t)row * ni + col] = tr[tx][ty + 8 * r];
+    Pt[(size_t)a * ni + b] = v;
   }
 }
 
@@ -819,23 +818,17 @@ struct PolPrep {
   float* d_part = nullptr;
   float* d_wt = nullptr;
   __half* d_ys = nullptr;
+  double* d_e = nullptr;
   int4* d_strips = nullptr;
-  int* d_strip_of = nullptr;
   double scale = 0.0;
 };
 
 static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   const int ni = c->ni, nib = (ni + 127) / 128, nb32 = (ni + 31) / 32;
-  // strips covering the upper triangle: rows of block i, columns [128 i, ni) in pieces <= 256
+  // strips covering E: rows of block i, columns [0, ni) in pieces <= 256
   std::vector<int4> strips;
-  std::vector<int> strip_of(nb32 * nb32, -1);
   for (int i = 0; i < nib; ++i)
-    for (int c0 = 128 * i; c0 < ni; c0 += 256) {
-      const int N = std::min(256, ni - c0);
-      for (int ab = 4 * i; ab < std::min(4 * i + 4, nb32); ++ab)
-        for (int bb = c0 / 32; bb < (c0 + N) / 32; ++bb) strip_of[ab * nb32 + bb] = (int)strips.size();
-      strips.push_back(make_int4(i, c0, N, 0));
-    }
+    for (int c0 = 0; c0 < ni; c0 += 256) strips.push_back(make_int4(i, c0, std::min(256, ni - c0), 0));
   const int nstrips = (int)strips.size();
   const int np = c->nb * c->nb, cpk = (np + 31) / 32, total = c->nk * cpk, npw = cpk * 32;
   // K segments. The tensor cores accumulate in FP32 with an error that grows with the
@@ -850,26 +843,27 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   while (base_units * nseg < 2 * sms && (total + nseg) / (nseg + 1) >= 4) ++nseg;
   // the partials of at most pol_part_bytes are held at once: segments run in passes, each
   // reduced into P (the first pass writes, later ones add)
-  const size_t seg_bytes = (size_t)base_units * 2 * 128 * 256 * sizeof(float);
+  const size_t seg_bytes = (size_t)base_units * P_TILE * sizeof(float);
   const int seg_pass = (int)std::max<size_t>(1, std::min<size_t>(nseg, c->pol_part_bytes / seg_bytes));
   const size_t part_bytes = seg_bytes * seg_pass;
   const size_t wt_bytes = (size_t)c->nk * c->ntau * npw * sizeof(float);
   const size_t ys_bytes = (size_t)c->nk * cpk * nib * 2 * 128 * 64 * sizeof(__half);
+  const size_t e_bytes = (size_t)c->ntau * ni * ni * sizeof(double);
   gw_status st;
-  if ((st = ensure(c, &c->mw.wslices, &c->mw.wslices_bytes, part_bytes + wt_bytes + ys_bytes, "P workspace")) != GW_OK)
+  if ((st = ensure(c, &c->mw.wslices, &c->mw.wslices_bytes, part_bytes + wt_bytes + ys_bytes + e_bytes,
+                   "P workspace")) != GW_OK)
     return st;
   float* d_part = (float*)c->mw.wslices;
   float* d_wt = d_part + part_bytes / sizeof(float);
   __half* d_ys = (__half*)((char*)d_wt + wt_bytes);
-  const size_t meta_bytes = sizeof(int4) * strips.size() + sizeof(int) * strip_of.size() + sizeof(int);
+  double* d_e = (double*)((char*)d_ys + ys_bytes);
+  const size_t meta_bytes = sizeof(int4) * strips.size();
   const void* meta_before = c->mw.dacc;
   if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P strips")) != GW_OK) return st;
   if (c->mw.dacc != meta_before) c->mw.strips_ready = false;
   int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
-  int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
   if (!c->mw.strips_ready) {  // depends on ni only: uploaded on the first call
-    if (cudaMemcpy(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(d_strips, strips.data(), meta_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
       return set_err(c, GW_ECUDA, "P strips upload");
     c->mw.strips_ready = true;
   }
@@ -893,17 +887,22 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   pp->d_part = d_part;
   pp->d_wt = d_wt;
   pp->d_ys = d_ys;
+  pp->d_e = d_e;
   pp->d_strips = d_strips;
-  pp->d_strip_of = d_strip_of;
   pp->scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
   return GW_OK;
 }
 
-// Sum the partials of the segments [s0, s0 + ns) into P (the first pass writes, later ones add).
+// Sum the partials of the segments [s0, s0 + ns) into E, then form P from E (the first pass writes
+// P, later ones add).
 static gw_status pol_reduce(gw_ctx* c, const PolPrep& pp, int s0, int ns, double* P) {
-  k_pol_reduce<<<dim3(pp.nb32 * (pp.nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(
-      pp.d_part, c->ni, c->ntau, pp.d_strip_of, pp.nstrips, pp.d_strips, ns, pp.scale, s0 > 0 ? 1 : 0, (double2*)P);
-  return check_launch(c, "pol_reduce");
+  k_pol_sum_e<<<dim3(pp.nstrips * 8, c->ntau), 256, 0, c->stream>>>(pp.d_part, c->ni, c->ntau, pp.nstrips,
+                                                                     pp.d_strips, ns, pp.d_e);
+  gw_status st = check_launch(c, "pol_sum_e");
+  if (st != GW_OK) return st;
+  k_pol_form<<<dim3(pp.nb32, pp.nb32, c->ntau), 256, 0, c->stream>>>(pp.d_e, c->ni, pp.scale, s0 > 0 ? 1 : 0,
+                                                                       (double2*)P);
+  return check_launch(c, "pol_form");
 }
 
 static size_t pol_smem() { return 1024 + 2 * P_STAGE_BYTES + sizeof(PolSmem); }
