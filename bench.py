@@ -167,10 +167,31 @@ def run_reference(args, cfg):
     print(json.dumps(out))
 
 
+def _gap_record(cfg, args, prec):
+    """The committed measurement of the QP-gap error of this chain against the FP64 chain
+    (`--config gapcheck`, profiles/gap_<cfg>.json), if it was taken on the current source of the
+    tensor-core kernels; else {}."""
+    p = os.path.join(ROOT, "profiles", f"gap_{cfg}.json")
+    src = os.path.join(ROOT, "paper_1602_02313_gb300", "csrc", "tc_mixed.cu")
+    if prec in ("fp64", "oracle") or not os.path.exists(p):
+        return {}
+    try:
+        d = json.load(open(p))
+        if d.get("src_sha") != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
+            return {}
+        chain = "mixed_" + getattr(args, "screen", "f32x2")
+        return {"gap_err_mev": {"cpe_ridge_1e-3": d["gap_err_mev"][chain + "/cpe_0.001"],
+                                "pade": d["gap_err_mev"][chain + "/pade"]},
+                "fp64_iteration_s": d["fp64_iteration_s"],
+                "gap_source": f"profiles/gap_{cfg}.json ({d['command']}, all {cfg} q)"}
+    except Exception:
+        return {}
+
+
 def _config(cfg, args, prec):
     import gwinputs as gi
     c = gi.CONFIGS[cfg]
-    return {"workload": f"synthetic crystal {cfg}: Nk={c['nk']} (q on the same grid), Nb={c['nb']} "
+    return {**_gap_record(cfg, args, prec), "workload": f"synthetic crystal {cfg}: Nk={c['nk']} (q on the same grid), Nb={c['nb']} "
                         f"({c['nocc']} occ), NI={c['ni']}, Ntau={c['ntau']}, Nnu=Nw={c['nnu']}, beta={c['beta']}",
             "precision": prec, "omega": args.omega, "continuation": getattr(args, "cont", "pade"),
             "screening": getattr(args, "screen", "f32x2") if prec != "fp64" else "fp64",
