@@ -950,12 +950,16 @@ def main():
             kern[name] = {"launches": n, "total_ms": tot, "avg_ms": tot / n}
     ctx.kernel_timing(False)
     per_launch_flops = {"polarization": fp, "selfenergy": fs, "k_pol_tc": fp, "k_sig_tc": fs}
-    # tensor-core MMA flops per algorithmic flop: 3 split products; P's 128-row strips cover the
-    # Hermitian half (NI^2 / 2) with sum_i 128 (NI - 128 i) outputs; Sigma runs 4 real GEMMs over
-    # the upper triangle of W~, (nkc + 1) / (2 nkc) of the columns, against 4 NI^2 MACs counted
+    # tensor-core MMA flops per algorithmic flop: 3 split products times the cover of P's strips;
+    # Sigma runs 4 real GEMMs over the upper triangle of W~, (nkc + 1) / (2 nkc) of the columns,
+    # against 4 NI^2 MACs counted
     ni_ = cr.ni
-    # P: E = Re P + Im P in strips of 128 rows over all NI columns (rows padded to 128)
-    strip_cover = 128 * ((ni_ + 127) // 128) / float(ni_)
+    # P up to NI = 256: E = Re P + Im P in strips of 128 rows over all NI columns (rows padded to
+    # 128); above: Re P and Im P over strips of the Hermitian half
+    if ni_ <= 256:
+        strip_cover = 128 * ((ni_ + 127) // 128) / float(ni_)
+    else:
+        strip_cover = sum(128 * (ni_ - 128 * i) for i in range((ni_ + 127) // 128)) / (ni_ * ni_ / 2.0)
     nkc_ = ni_ // 32
     mma_factor = {"k_pol_tc": 3.0 * strip_cover, "k_sig_tc": 3.0 * (nkc_ + 1) / (2.0 * nkc_)}
     peaks = _peaks()

@@ -11,10 +11,13 @@
 //   P(tau) is Hermitian (w is real), so the real matrix E = Re P + Im P holds all of it:
 //   Re P = (E + E^T) / 2, Im P = (E - E^T) / 2. E is one real GEMM, E = X Y^T with rows
 //   X_I = [w (Re A_I + Im A_I) | w (Im A_I - Re A_I)], Y_I' = [Re A_I' | Im A_I']: tiles of E
-//   cover NI^2 exactly (the Hermitian half in strips of 128 rows would cover 1.5x of it).
-//   Work unit = (K segment, 128-row strip of <= 256 columns of E, tau); the FP32 partial strips
-//   are summed over K segments with float-float accumulators into E (FP64) by a second kernel,
-//   and a third forms Re P and Im P.
+//   cover NI^2 exactly (the Hermitian half in strips of 128 rows covers 1.5x of it at NI = 256).
+//   This E form is used up to NI = 256. Above, the complex form: Re P = X Y^T, Im P = X' Y^T with
+//   rows X_I = [w Re A_I | w Im A_I], X'_I = [w Im A_I | -w Re A_I] (the same shared-memory tile,
+//   other K halves, negated) over strips of the Hermitian half, two accumulators per X build.
+//   Work unit = (K segment, 128-row strip of <= 256 columns, tau); the FP32 partial strips are
+//   summed over K segments with float-float accumulators by a second kernel (into E in FP64, and
+//   a third forms P; or directly into P, writing the lower triangle too).
 //
 // self-energy, Eq. (sigc), one q:
 //   d_p(tau) = a_p^H W~(tau) a_p = Re a_p^T Wr Re a_p + Im a_p^T Wr Im a_p + 2 Im a_p^T Wi Re a_p
@@ -83,12 +86,13 @@ struct alignas(16) h8 {
 
 // --------------------------------------------------------------------------- polarization
 // E is covered by "strips": rows [128 i, 128 i + 128) x columns [c0, c0 + N), c0 = 0, 256, ...,
-// N <= 256. A work unit is (K segment, strip, tau). The unscaled
+// N <= 256 (the upper triangle of P in the complex form: c0 = 128 i, 128 i + 256, ...). A work
+// unit is (K segment, strip, tau). The unscaled
 // operand Y (rows of the strip's columns) is bulk-copied from YS, a pre-split,
 // pre-swizzled image of M[q]:
 //   YS[k][chunk][iblk][slice][128 rows x 128 B], row = [Re A (32 pairs) | Im A (32 pairs)],
 // slices hi, lo. The scaled operand X (rows of the strip) is built by the producer warps from the
-// same image. TMEM holds E (N columns).
+// same image. TMEM holds E (N columns), or Re P and Im P (N columns each).
 constexpr int kPolChunksPerSeg = 32;  // upper bound of the context's K chunks per segment
 constexpr int PT_THREADS = 288;                     // warps 0-7 produce / run the epilogue, warp 8 issues MMAs
 constexpr int P_XT = 16384;                         // one X slice: 128 rows x 128 B
@@ -157,6 +161,7 @@ struct PolJob {
   float* part;
   const int4* strips;
   int nk, ni, ntau, cpk, npw, nstrips, nseg, seg0;
+  int eform;  // 1: strips of E (one accumulator); 0: strips of the Hermitian half (Re P, Im P)
   int units;  // K segments x strips x tau of this job (this launch's segments)
 };
 
@@ -258,8 +263,8 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
         for (int e = 0; e < 8; ++e) {
           const float re = __half2float(cur[j].rh.v[e]) + __half2float(cur[j].rl.v[e]);
           const float im = __half2float(cur[j].ih.v[e]) + __half2float(cur[j].il.v[e]);
-          split2(wv[e] * (re + im), orh.v[e], orl.v[e]);
-          split2(wv[e] * (im - re), oih.v[e], oil.v[e]);
+          split2(wv[e] * (J.eform ? re + im : re), orh.v[e], orl.v[e]);
+          split2(wv[e] * (J.eform ? im - re : im), oih.v[e], oil.v[e]);
         }
         *reinterpret_cast<h8*>(st + oRe) = orh;
         *reinterpret_cast<h8*>(st + oIm) = oih;
@@ -273,7 +278,8 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
     }
   } else if (lane == 0) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t id = idesc_f16(128, N, false, false);
+    const uint32_t id = idesc_f16(128, N, false, false), idn = idesc_f16(128, N, false, true);
+    const uint32_t dim = tbase + N;  // Im P (complex form)
     if (stall && ph.units == 0) wait_bar(&S.never, 0, &S.abort_flag, err, wait_cycles);  // injected stall
     for (int i = 0; i < nchunk; ++i) {
       const int ic = ph.cbase + i, s = ic & 1;
@@ -288,6 +294,14 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
         mma_f16(tbase, sdesc_sw128(xh + bo), sdesc_sw128(yh + bo), id, acc);
         mma_f16(tbase, sdesc_sw128(xh + bo), sdesc_sw128(yl + bo), id, 1);
         mma_f16(tbase, sdesc_sw128(xl + bo), sdesc_sw128(yh + bo), id, 1);
+        if (!J.eform) {
+          // Im P = [w Im A | -w Re A] . [Re A | Im A]: other K half of X, negated for the second half
+          const uint32_t ao = 32 * ((ks + 2) & 3);
+          const uint32_t idx = ks < 2 ? id : idn;
+          mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yh + bo), idx, acc);
+          mma_f16(dim, sdesc_sw128(xh + ao), sdesc_sw128(yl + bo), idx, 1);
+          mma_f16(dim, sdesc_sw128(xl + ao), sdesc_sw128(yh + bo), idx, 1);
+        }
       }
       mma_commit(&S.empty[s]);
     }
@@ -301,19 +315,24 @@ __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, uns
     tc_fence_after();
     const int quad = warp & 3, half = warp >> 2;
     const int row = 32 * quad + lane;
-    float* out = J.part + (size_t)u * P_TILE + (size_t)row * 256;
+    const int nacc = J.eform ? 1 : 2;
+    float* out = J.part + (size_t)u * nacc * P_TILE + (size_t)row * 256;
     const int nb16 = N / 16;
-    for (int bk = half; bk < nb16; bk += 2) {
-      float v[16];
-      if (ok) {
-        tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + 16 * bk, v);
-      } else {
+    const int ab = 4 * xb + quad;  // the 32-row block of this warp's rows
+    for (int acc = 0; acc < nacc; ++acc) {
+      for (int bk = half; bk < nb16; bk += 2) {
+        if (!J.eform && ((c0 + 16 * bk) >> 5) < ab) continue;  // below the diagonal: never read back
+        float v[16];
+        if (ok) {
+          tmem_ld16(tbase + ((uint32_t)(32 * quad) << 16) + acc * N + 16 * bk, v);
+        } else {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = 0.f;
+          for (int e = 0; e < 16; ++e) v[e] = 0.f;
+        }
+        float4* o = reinterpret_cast<float4*>(out + (size_t)acc * P_TILE + 16 * bk);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
       }
-      float4* o = reinterpret_cast<float4*>(out + 16 * bk);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) o[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
     }
     tc_fence_before();
   }
@@ -362,7 +381,8 @@ __device__ __forceinline__ void pol_block_finish(PolSmem& S, uint32_t tbase, int
 // One work unit per block: the units of one (context, q).
 __global__ void __launch_bounds__(PT_THREADS, 1)
     k_pol_tc(const __half* __restrict__ YS, const float* __restrict__ wt, int nk, int ni, int ntau, int cpk,
-             int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, float* __restrict__ part,
+             int npw, int nstrips, const int4* __restrict__ strips, int nseg, int seg0, int eform,
+             float* __restrict__ part,
              int* __restrict__ err, long long wait_cycles, int stall) {
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -370,7 +390,7 @@ __global__ void __launch_bounds__(PT_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   pol_block_init(S, tid, warp);
   const uint32_t tbase = S.tslot;
-  PolJob J{YS, wt, part, strips, nk, ni, ntau, cpk, npw, nstrips, nseg, seg0, 0};
+  PolJob J{YS, wt, part, strips, nk, ni, ntau, cpk, npw, nstrips, nseg, seg0, eform, 0};
   PolPhase ph;
   pol_unit(J, blockIdx.x, S, base, tbase, tid, warp, lane, ph, err, wait_cycles, stall);
   // the epilogue has seen the unit's `done` phase before the MMA thread commits `done` again in
@@ -420,6 +440,68 @@ __device__ __forceinline__ void two_sum_acc(float& h, float& l, float x) {
   const float v = s - h;
   l += (h - (s - v)) + (x - v);
   h = s;
+}
+
+// Complex form: sum the FP32 partial strips of Re P and Im P over K segments and write the
+// Hermitian P (FP64).
+// One block per (32 x 32 block (ab, bb) with ab <= bb, tau); reads are coalesced along
+// the column, the mirrored lower triangle is written through a shared-memory transpose.
+__global__ void __launch_bounds__(256) k_pol_reduce(const float* __restrict__ part, int ni, int ntau,
+                                                    const int* __restrict__ strip_of, int nstrips,
+                                                    const int4* __restrict__ strips, int nseg, double scale,
+                                                    int accumulate, double2* __restrict__ P) {
+  __shared__ double2 tr[32][33];
+  const int nb32 = (ni + 31) / 32;
+  int t = blockIdx.x, ab = 0;
+  while (t >= nb32 - ab) {
+    t -= nb32 - ab;
+    ++ab;
+  }
+  const int bb = ab + t;
+  const int it = blockIdx.y;
+  const int strip = strip_of[ab * nb32 + bb];
+  const int4 sd = strips[strip];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int b = bb * 32 + tx;
+  // float-float accumulators (hi + lo, error-free two-sum per addition): as exact as an FP64
+  // sum of these FP32 terms to ~2^-44, on the FP32 pipes (GB300's FP64 rate is ~1/64 of FP32)
+  float reh[4] = {0, 0, 0, 0}, rel[4] = {0, 0, 0, 0}, imh[4] = {0, 0, 0, 0}, iml[4] = {0, 0, 0, 0};
+  size_t o[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) o[r] = (size_t)((ab * 32 + ty + 8 * r) & 127) * 256 + (b - sd.y);
+  const size_t ustride = (size_t)nstrips * ntau * 2 * 128 * 256;  // one K segment further
+  const float* pre = part + ((size_t)strip * ntau + it) * 2 * 128 * 256;
+#pragma unroll 2
+  for (int s = 0; s < nseg; ++s, pre += ustride) {
+    const float* pim = pre + 128 * 256;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      two_sum_acc(reh[r], rel[r], pre[o[r]]);
+      two_sum_acc(imh[r], iml[r], pim[o[r]]);
+    }
+  }
+  double2* Pt = P + (size_t)it * ni * ni;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int a = ab * 32 + ty + 8 * r;
+    double2 v = make_double2(((double)reh[r] + (double)rel[r]) * scale, ((double)imh[r] + (double)iml[r]) * scale);
+    if (a == b) v.y = 0.0;  // Im P_II = 0 exactly (the tensor-core sum leaves O(2^-22) residue)
+    if (accumulate && a < ni && b < ni) {  // a later pass over K segments: add to the earlier sum
+      const double2 o = Pt[(size_t)a * ni + b];
+      v.x += o.x;
+      v.y += o.y;
+    }
+    if (a < ni && b < ni && (ab < bb || a <= b)) Pt[(size_t)a * ni + b] = v;
+    tr[ty + 8 * r][tx] = make_double2(v.x, -v.y);
+  }
+  __syncthreads();
+  // lower triangle: P[b'][a'] = conj(P[a'][b']) for a' < b'
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int row = bb * 32 + ty + 8 * r;  // b'
+    const int col = ab * 32 + tx;          // a'
+    if (row < ni && col < ni && col < row) Pt[(size_t)row * ni + col] = tr[tx][ty + 8 * r];
+  }
 }
 
 // Sum the FP32 partial strips of E over K segments into E (FP64), one block per (strip, 16-row
@@ -814,21 +896,36 @@ int num_sms(gw_ctx* c) {
 // Host plan of one polarization job: strips, K segments, workspace, and the operand image and
 // pair weights of its q, built on the context's stream.
 struct PolPrep {
-  int nstrips = 0, nseg = 0, seg_pass = 0, base_units = 0, nb32 = 0, cpk = 0, npw = 0;
+  int nstrips = 0, nseg = 0, seg_pass = 0, base_units = 0, nb32 = 0, cpk = 0, npw = 0, eform = 1;
   float* d_part = nullptr;
   float* d_wt = nullptr;
   __half* d_ys = nullptr;
   double* d_e = nullptr;
   int4* d_strips = nullptr;
+  int* d_strip_of = nullptr;
   double scale = 0.0;
 };
 
 static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   const int ni = c->ni, nib = (ni + 127) / 128, nb32 = (ni + 31) / 32;
-  // strips covering E: rows of block i, columns [0, ni) in pieces <= 256
+  // Which form: the producers' X builds pace the E form (one accumulator per build) and the MMAs
+  // the complex form (Re P and Im P from one build). Per (k, tau, chunk), E needs nib ceil(ni / 256)
+  // builds and 3 ni (128 nib) MMA columns, the complex form one build per strip of the Hermitian
+  // half and 6 x its columns; E is the faster one up to ni = 256 (2 builds either way at 256, a
+  // third less MMA work), the complex one above (at 512: 8 builds against 6).
+  const int eform = ni <= 256 ? 1 : 0;
+  // strips covering E: rows of block i, columns [0, ni) in pieces <= 256; or covering the upper
+  // triangle of P: rows of block i, columns [128 i, ni) in pieces <= 256
   std::vector<int4> strips;
+  std::vector<int> strip_of(eform ? 0 : nb32 * nb32, -1);
   for (int i = 0; i < nib; ++i)
-    for (int c0 = 0; c0 < ni; c0 += 256) strips.push_back(make_int4(i, c0, std::min(256, ni - c0), 0));
+    for (int c0 = eform ? 0 : 128 * i; c0 < ni; c0 += 256) {
+      const int N = std::min(256, ni - c0);
+      if (!eform)
+        for (int ab = 4 * i; ab < std::min(4 * i + 4, nb32); ++ab)
+          for (int bb = c0 / 32; bb < (c0 + N) / 32; ++bb) strip_of[ab * nb32 + bb] = (int)strips.size();
+      strips.push_back(make_int4(i, c0, N, 0));
+    }
   const int nstrips = (int)strips.size();
   const int np = c->nb * c->nb, cpk = (np + 31) / 32, total = c->nk * cpk, npw = cpk * 32;
   // K segments. The tensor cores accumulate in FP32 with an error that grows with the
@@ -843,12 +940,12 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   while (base_units * nseg < 2 * sms && (total + nseg) / (nseg + 1) >= 4) ++nseg;
   // the partials of at most pol_part_bytes are held at once: segments run in passes, each
   // reduced into P (the first pass writes, later ones add)
-  const size_t seg_bytes = (size_t)base_units * P_TILE * sizeof(float);
+  const size_t seg_bytes = (size_t)base_units * (eform ? 1 : 2) * P_TILE * sizeof(float);
   const int seg_pass = (int)std::max<size_t>(1, std::min<size_t>(nseg, c->pol_part_bytes / seg_bytes));
   const size_t part_bytes = seg_bytes * seg_pass;
   const size_t wt_bytes = (size_t)c->nk * c->ntau * npw * sizeof(float);
   const size_t ys_bytes = (size_t)c->nk * cpk * nib * 2 * 128 * 64 * sizeof(__half);
-  const size_t e_bytes = (size_t)c->ntau * ni * ni * sizeof(double);
+  const size_t e_bytes = eform ? (size_t)c->ntau * ni * ni * sizeof(double) : 0;
   gw_status st;
   if ((st = ensure(c, &c->mw.wslices, &c->mw.wslices_bytes, part_bytes + wt_bytes + ys_bytes + e_bytes,
                    "P workspace")) != GW_OK)
@@ -857,13 +954,16 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   float* d_wt = d_part + part_bytes / sizeof(float);
   __half* d_ys = (__half*)((char*)d_wt + wt_bytes);
   double* d_e = (double*)((char*)d_ys + ys_bytes);
-  const size_t meta_bytes = sizeof(int4) * strips.size();
+  const size_t meta_bytes = sizeof(int4) * strips.size() + sizeof(int) * strip_of.size();
   const void* meta_before = c->mw.dacc;
   if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P strips")) != GW_OK) return st;
   if (c->mw.dacc != meta_before) c->mw.strips_ready = false;
   int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
+  int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
   if (!c->mw.strips_ready) {  // depends on ni only: uploaded on the first call
-    if (cudaMemcpy(d_strips, strips.data(), meta_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!strip_of.empty() && cudaMemcpy(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(),
+                                         cudaMemcpyHostToDevice) != cudaSuccess))
       return set_err(c, GW_ECUDA, "P strips upload");
     c->mw.strips_ready = true;
   }
@@ -889,6 +989,8 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   pp->d_ys = d_ys;
   pp->d_e = d_e;
   pp->d_strips = d_strips;
+  pp->d_strip_of = d_strip_of;
+  pp->eform = eform;
   pp->scale = 1.0 / ((double)kScaleA * kScaleA * c->omega * c->nk);
   return GW_OK;
 }
@@ -896,6 +998,12 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
 // Sum the partials of the segments [s0, s0 + ns) into E, then form P from E (the first pass writes
 // P, later ones add).
 static gw_status pol_reduce(gw_ctx* c, const PolPrep& pp, int s0, int ns, double* P) {
+  if (!pp.eform) {
+    k_pol_reduce<<<dim3(pp.nb32 * (pp.nb32 + 1) / 2, c->ntau), 256, 0, c->stream>>>(
+        pp.d_part, c->ni, c->ntau, pp.d_strip_of, pp.nstrips, pp.d_strips, ns, pp.scale, s0 > 0 ? 1 : 0,
+        (double2*)P);
+    return check_launch(c, "pol_reduce");
+  }
   k_pol_sum_e<<<dim3(pp.nstrips * 8, c->ntau), 256, 0, c->stream>>>(pp.d_part, c->ni, c->ntau, pp.nstrips,
                                                                      pp.d_strips, ns, pp.d_e);
   gw_status st = check_launch(c, "pol_sum_e");
@@ -919,7 +1027,8 @@ gw_status launch_pol_mixed(gw_ctx* c, int iq, const double* G, int prec, double*
     kt_begin(c, "k_pol_tc");
     k_pol_tc<<<pp.base_units * ns, PT_THREADS, smem, c->stream>>>(pp.d_ys, pp.d_wt, c->nk, c->ni, c->ntau, pp.cpk,
                                                                   pp.npw, pp.nstrips, pp.d_strips, pp.nseg, s0,
-                                                                  pp.d_part, c->d_err, c->wait_cycles, c->fault_stall);
+                                                                  pp.eform, pp.d_part, c->d_err, c->wait_cycles,
+                                                                  c->fault_stall);
     kt_end(c);
     if ((st = check_launch(c, "pol_tc")) != GW_OK) return st;
     if ((st = pol_reduce(c, pp, s0, ns, P)) != GW_OK) return st;
@@ -955,7 +1064,7 @@ gw_status launch_pol_many(int njobs, gw_ctx* const* ctxs, const int* iqs, const 
       gw_ctx* c = ctxs[j];
       PolJob& J = Q.job[Q.njobs++];
       J = PolJob{pp[j].d_ys, pp[j].d_wt, pp[j].d_part, pp[j].d_strips, c->nk, c->ni, c->ntau, pp[j].cpk,
-                 pp[j].npw, pp[j].nstrips, pp[j].nseg, s0[j], pp[j].base_units * ns};
+                 pp[j].npw, pp[j].nstrips, pp[j].nseg, s0[j], pp[j].eform, pp[j].base_units * ns};
       Q.total += J.units;
       jid.push_back(j);
       nsj.push_back(ns);
