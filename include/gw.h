@@ -401,13 +401,17 @@ gw_status gw_set_stream(gw_ctx* ctx, void* stream);
  *      ~2 s at the GPU's top clock; a healthy wait takes microseconds);
  *  GW_TUNE_FAULT_STALL: fault injection for tests of that detector, 0 or 1: with 1, the
  *      MMA-issuing thread of every tensor-core contraction block first waits on a barrier that
- *      nothing arrives on, so the wait runs out after the wait budget (the GPU stays usable).
+ *      nothing arrives on, so the wait runs out after the wait budget (the GPU stays usable);
+ *  GW_TUNE_POL_FORM: how the tensor-core polarization covers the Hermitian P(tau): 0 = by ni (the
+ *      default: the real matrix E = Re P + Im P for ni <= 256, Re P and Im P over the Hermitian
+ *      half above), 1 = always E, 2 = always Re P and Im P. Both give P within the same bound.
  * Out-of-range values return GW_EINVAL. Results stay within the tensor-core error bound. */
 typedef enum {
   GW_TUNE_POL_SEG_CHUNKS = 0,
   GW_TUNE_POL_PART_MB = 1,
   GW_TUNE_WAIT_CYCLES = 2,
-  GW_TUNE_FAULT_STALL = 3
+  GW_TUNE_FAULT_STALL = 3,
+  GW_TUNE_POL_FORM = 4
 } gw_tune;
 gw_status gw_set_tuning(gw_ctx* ctx, gw_tune key, int64_t value);
 gw_status gw_kernel_time(gw_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);

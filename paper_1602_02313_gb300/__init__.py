@@ -24,7 +24,7 @@ GW_FP64, GW_FP16X2, GW_F32X2, GW_F32 = 0, 1, 3, 4
 GW_BOSE, GW_FERMI = 0, 1
 GW_TAU_TO_IW, GW_IW_TO_TAU, GW_TAU_TO_IW_CONT = 0, 1, 2
 GW_PADE, GW_CPE = 0, 1
-GW_TUNE_POL_SEG_CHUNKS, GW_TUNE_POL_PART_MB, GW_TUNE_WAIT_CYCLES, GW_TUNE_FAULT_STALL = 0, 1, 2, 3
+GW_TUNE_POL_SEG_CHUNKS, GW_TUNE_POL_PART_MB, GW_TUNE_WAIT_CYCLES, GW_TUNE_FAULT_STALL, GW_TUNE_POL_FORM = 0, 1, 2, 3, 4
 PREC = {"fp64": GW_FP64, "fp16x2": GW_FP16X2}
 
 _STATUS = {0: "GW_OK", -1: "GW_EINVAL", -2: "GW_ENOMEM", -3: "GW_ECUDA", -4: "GW_ESINGULAR",

@@ -885,6 +885,10 @@ gw_status gw_set_tuning(gw_ctx* c, gw_tune key, int64_t value) {
       if (value != 0 && value != 1) return set_err(c, GW_EINVAL, "gw_set_tuning: stall injection is 0 or 1");
       c->fault_stall = (int)value;
       return GW_OK;
+    case GW_TUNE_POL_FORM:
+      if (value < 0 || value > 2) return set_err(c, GW_EINVAL, "gw_set_tuning: polarization form is 0, 1 or 2");
+      c->pol_form = (int)value;
+      return GW_OK;
   }
   return set_err(c, GW_EINVAL, "gw_set_tuning: unknown key");
 }

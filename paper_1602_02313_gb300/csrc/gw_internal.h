@@ -40,6 +40,7 @@ struct MixedWork {
   double* dacc = nullptr;     // P strip metadata (uploaded once per context) and error word
   size_t dacc_bytes = 0;
   bool strips_ready = false;
+  int strips_form = -1;       // the form the uploaded strips were built for
 };
 
 }  // namespace gwi
@@ -118,6 +119,7 @@ struct gw_ctx {
   int* d_err = nullptr;                     // error word of the bounded device waits (read by gw_sync)
   long long wait_cycles = 4000000000ll;     // clock cycles a tensor-core pipeline wait may take (~2 s)
   int fault_stall = 0;                      // test fault injection: MMA issuers wait on a barrier nothing sets
+  int pol_form = 0;                         // polarization cover: 0 by ni, 1 E = Re P + Im P, 2 Re P and Im P
   int pol_seg_chunks = 32;                  // K chunks per FP32 accumulation segment of P (<= 32)
   size_t pol_part_bytes = 8ull << 30;       // FP32 partial strips of P held at once
   // per-kernel timing (gw_kernel_timing): CUDA events recorded around selected launches

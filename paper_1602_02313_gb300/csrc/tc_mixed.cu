@@ -913,7 +913,7 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   // builds and 3 ni (128 nib) MMA columns, the complex form one build per strip of the Hermitian
   // half and 6 x its columns; E is the faster one up to ni = 256 (2 builds either way at 256, a
   // third less MMA work), the complex one above (at 512: 8 builds against 6).
-  const int eform = ni <= 256 ? 1 : 0;
+  const int eform = c->pol_form == 1 ? 1 : c->pol_form == 2 ? 0 : (ni <= 256 ? 1 : 0);
   // strips covering E: rows of block i, columns [0, ni) in pieces <= 256; or covering the upper
   // triangle of P: rows of block i, columns [128 i, ni) in pieces <= 256
   std::vector<int4> strips;
@@ -957,15 +957,16 @@ static gw_status pol_prepare(gw_ctx* c, int iq, const double* G, PolPrep* pp) {
   const size_t meta_bytes = sizeof(int4) * strips.size() + sizeof(int) * strip_of.size();
   const void* meta_before = c->mw.dacc;
   if ((st = ensure(c, (void**)&c->mw.dacc, &c->mw.dacc_bytes, meta_bytes + 256, "P strips")) != GW_OK) return st;
-  if (c->mw.dacc != meta_before) c->mw.strips_ready = false;
+  if (c->mw.dacc != meta_before || c->mw.strips_form != eform) c->mw.strips_ready = false;
   int4* d_strips = reinterpret_cast<int4*>(c->mw.dacc);
   int* d_strip_of = reinterpret_cast<int*>(d_strips + strips.size());
-  if (!c->mw.strips_ready) {  // depends on ni only: uploaded on the first call
+  if (!c->mw.strips_ready) {  // depends on ni and the form: uploaded on the first call of each
     if (cudaMemcpy(d_strips, strips.data(), sizeof(int4) * strips.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         (!strip_of.empty() && cudaMemcpy(d_strip_of, strip_of.data(), sizeof(int) * strip_of.size(),
                                          cudaMemcpyHostToDevice) != cudaSuccess))
       return set_err(c, GW_ECUDA, "P strips upload");
     c->mw.strips_ready = true;
+    c->mw.strips_form = eform;
   }
   if (ni % 128) cudaMemsetAsync(d_ys, 0, ys_bytes, c->stream);  // rows >= ni of the last block stay zero
   const double2* Mq = (const double2*)m_block(c, iq);

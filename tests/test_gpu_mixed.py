@@ -96,6 +96,47 @@ def test_selfenergy_tc(gw, name, case):
     assert ex < TOL_SX_FF
 
 
+def test_polarization_forms(gw):
+    """Both covers of the Hermitian P, forced with GW_TUNE_POL_FORM on one context: the real
+    matrix E = Re P + Im P (1) and Re P / Im P over the Hermitian half (2), at NI = 160 against the
+    oracle, at NI = 256 and 384 against the FP64 GPU path, switching forms back and forth (the strip
+    metadata is rebuilt for each); the default (0) takes E up to NI = 256."""
+    cases_ = [("ni160", gi.make_crystal(78, 8, 12, 5, 160, 50.0, qlist=[3]), gi.make_grid(50.0, 12, 12, 12, ncont=24),
+               True),
+              ("ni256", *gi.make_config("nk64_nb64", nk=8, qlist=[3]), False),
+              ("ni384", gi.make_crystal(79, 8, 24, 10, 384, 80.0, qlist=[2]), gi.make_grid(80.0, 16, 16, 16, ncont=24),
+               False)]
+    for name, cr, gr, with_oracle in cases_:
+        ctx = gw.GW(gr, cr, omega=1.0)
+        G, _ = orc.green_tau0(cr.eps, gr.tau, gr.beta)
+        Gd = dev(G)
+        if with_oracle:
+            ref = orc.polarization(gi.m_for_q(cr, 0), G, cr.kmq[0])
+        else:
+            P64 = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+            ctx.polarization(0, Gd, P64, gw.GW_FP64)
+            ctx.sync()
+            ref = host(P64)
+        out = {}
+        for form in (1, 2, 1, 0):
+            ctx.set_tuning(gw.GW_TUNE_POL_FORM, form)
+            P = zeros((gr.ntau, cr.ni, cr.ni), "c16")
+            ctx.polarization(0, Gd, P, gw.GW_FP16X2)
+            ctx.sync()
+            Ph = host(P)
+            e = rel(Ph, ref)
+            print(f"{name} form {form}: P tensor-core rel err {e:.3e}")
+            assert e < TOL_P
+            assert np.abs(Ph - np.conj(np.swapaxes(Ph, 1, 2))).max() == 0.0
+            if form in out:
+                assert np.array_equal(out[form], Ph)  # the same form twice: the same bits
+            out[form] = Ph
+        assert np.array_equal(out[0], out[1] if cr.ni <= 256 else out[2])
+        with pytest.raises(gw.GwError):
+            ctx.set_tuning(gw.GW_TUNE_POL_FORM, 3)
+        ctx.close()
+
+
 def test_c2_full_size_tc_vs_fp64(gw):
     """Bench sizes (Nk = 64, Nb = 64, NI = 256, Ntau = 48), in the bench's launch configuration:
     tensor-core P and Sigma of one q against the FP64 GPU path everywhere, and against the oracle
