@@ -240,7 +240,7 @@ def run_batch(args, prec):
     shapes = [f"Nk={cr.nk} Nb={cr.nb} NI={cr.ni} Ntau={len(gr.tau)} beta={gr.beta}" for cr, gr in systems]
     out = {"metric": METRIC + " (batch of 12 crystals)", "value": batch.flops / (best_ms * 1e-3) / 1e12,
            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": best_ms,
-           "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "fp16x2 split (fp32 accum) + f64",
+           "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": _dtype(args),
            "data": "synthetic",
            "config": {"workload": "batch of 12 heterogeneous synthetic crystals: " + "; ".join(shapes),
                       "sequential_ms": seq_ms, "graph_ms": graph_ms, "queued_graph_ms": queued_ms,
@@ -451,7 +451,7 @@ def run_sym(args, prec):
     ms_red, S_red, E_red = res["irreducible"]
     out = {"metric": "symmetry-reduced G0W0 iteration time (Sec. III.C)", "value": ms_red, "unit": "ms",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_red, "higher_is_better": False,
-           "scaling": "strong", "vs_baseline": None, "dtype": "fp16x2 split (fp32 accum) + f64", "data": "synthetic",
+           "scaling": "strong", "vs_baseline": None, "dtype": _dtype(args), "data": "synthetic",
            "config": {"workload": f"synthetic Oh crystal: 4x4x4 mesh, Nb={c.nb} ({c.nocc} occ), NI={c.ni}, "
                                   f"Ntau={len(gr.tau)}, beta={c.beta}; {len(c.ibz)} irreducible of {c.nq} q",
                       "full_mesh_ms": ms_full, "speedup": ms_full / ms_red,
