@@ -175,9 +175,10 @@ struct PolPhase {
   int last1 = -1;
 };
 
-// One work unit u of job J = (K segment, 128 x N strip of E, tau): the producer warps build
-// X = [w (Re A + Im A) | w (Im A - Re A)] and bring Y by bulk copy, one thread issues the MMAs, the producer
-// warps then move the FP32 partial strip out of TMEM. A wait that runs out raises S.abort_flag.
+// One work unit u of job J = (K segment, 128 x N strip, tau): the producer warps build
+// X = [w (Re A + Im A) | w (Im A - Re A)] (E form) or [w Re A | w Im A] (complex form) and bring Y
+// by bulk copy, one thread issues the MMAs, the producer warps then move the FP32 partial strip out
+// of TMEM. A wait that runs out raises S.abort_flag.
 __device__ __forceinline__ void pol_unit(const PolJob& J, int u, PolSmem& S, unsigned char* base, uint32_t tbase,
                                          int tid, int warp, int lane, PolPhase& ph, int* err, long long wait_cycles,
                                          int stall) {
